@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""FFT EnKF analysis benchmark: grid-pts x members per second at 4096^2, N=20.
+
+Workload (one "step" = one complete analysis, Sec. 2.1 eq. spectral-multi-enkf):
+4 blocks on a 4096 x 4096 periodic grid, 20 members, Matern-3/2 fields with
+length scales 8..128 cells correlated 0.6 through a shared latent field, BF16
+storage of members and perturbations, blocks 0 and 1 observed with
+rhat = 0.1/max(|k|,1).  Inputs are drawn on the device once; every timed step
+re-analyses the ensemble in place (2.7 GB of members, larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one full-size 4096^2 oracle DFT per step, scaled to the analysis's
+200 transforms).  Under torchrun every rank analyses its own independent
+problem (no collective on the data path, weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NY = NX = 4096
+M, N, N_OBS = 4, 20, 2
+OBSERVED = (1, 1, 0, 0)
+METRIC = "FFT-EnKF analysis grid-pts×members/s at 4096², N=20; % of HBM roofline"
+UNIT = "grid-pts*members/s"
+WORKLOAD = "FFT EnKF analysis, 4 blocks 4096x4096, N=20, BF16 storage, 2 observed (Matern-3/2, rhat~1/|k|)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--members", type=int, default=N)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def hbm_peak():
+    pk = peaks()
+    if "hbm_gbs" in pk:
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ byte model
+def pass_bytes(ny, nx, M, N, n_obs, s):
+    """Algorithmic HBM bytes of one launch of every pass (what the pass must move)."""
+    G = ny * nx
+    L = nx // 2
+    K1 = (L + 1) * ny
+    line = L * ny * 8                 # one field's packed row spectra, complex float
+    n_un = M - n_obs
+    nf = n_obs + 2 * n_obs * n_un     # floats per wavenumber of the covariance / gain tables
+    return {
+        "mean": M * N * G * s + M * G * 4,
+        "row_fwd_anomaly": M * N * G * s + M * G * 4 + M * N * line,
+        "col_stats": M * N * line + nf * K1 * 4,
+        "gain": nf * K1 * 4 + n_obs * K1 * 8 + nf * K1 * 4,
+        "row_fwd_innovation": 2 * n_obs * N * G * s + n_obs * G * 4 + n_obs * N * line,
+        "col_update": n_obs * N * line + nf * K1 * 4 + M * N * line,
+        "row_inv": M * N * line + 2 * M * N * G * s,
+    }
+
+
+def analysis_bytes(ny, nx, M, N, n_obs, s):
+    """The analysis's algorithmic bytes without the separate mean pass (ensemble read for
+    chat and for the update, innovations, data, rhat, gains written+read, output,
+    one write+read of every transform's intermediate)."""
+    G = ny * nx
+    K = ny * (nx // 2 + 1)
+    n_un = M - n_obs
+    return (2 * M * N * G * s + n_obs * N * G * s + n_obs * N * G * s + n_obs * G * 4 + n_obs * K * 8
+            + 2 * (n_obs * K * 4 + n_un * n_obs * K * 8) + M * N * G * s + (2 * M * N + n_obs * N) * 2 * K * 8)
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(pass_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+    except Exception:
+        return None
+    ent = t.get(pass_name)
+    if not ent or ent.get("source_sha") != source_sha():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1001_1588_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------ oracle (CPU) baseline
+def oracle_sample(ny, nx, n_transforms, seed=7):
+    """Time n_transforms full-size oracle 2-D DFTs (dense DFT-matrix products in FP64),
+    alternating forward and inverse."""
+    import numpy as np
+    from oracle import dft
+    u = np.random.default_rng(seed).standard_normal((ny, nx))
+    t0 = time.perf_counter()
+    U = u
+    for i in range(n_transforms):
+        U = dft.fft2(U) if i % 2 == 0 else dft.ifft2(U)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(ny, nx, M_, N_, n_obs, seconds_per_transform):
+    """Metric of the oracle: one analysis costs (2 M N + n_obs N) full-size transforms."""
+    transforms = 2 * M_ * N_ + n_obs * N_
+    t = transforms * seconds_per_transform
+    return ny * nx * N_ / t, transforms
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(int(i.get("num_threads", 1)) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(a.warmup):
+        oracle_sample(a.ny, a.nx, 1)
+    total = 0.0
+    for _ in range(a.steps):
+        total += oracle_sample(a.ny, a.nx, 1)
+    spt = total / a.steps
+    rate, transforms = oracle_rate(a.ny, a.nx, M, a.members, N_OBS, spt)
+    sample = ("one full-size %dx%d oracle DFT per step (dense DFT-matrix products, FP64); an analysis "
+              "is %d such transforms, the per-wavenumber work is O(G) and not counted" % (a.ny, a.nx, transforms))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": spt * transforms * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [a.ny, a.nx], "members": a.members,
+                                        "blocks": M, "observed": N_OBS},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1001_1588_gb300 import abi, torch_api
+    from synth.fields_torch import make_config3_torch
+
+    ny, nx, Nm = a.ny, a.nx, a.members
+    prob = make_config3_torch(device=dev, seed=20260003 + 1000 * rank, ny=ny, nx=nx, N=Nm)
+    plan = torch_api.Plan(ny, nx, M, Nm, torch.bfloat16, OBSERVED)
+    plan.workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.analyze(prob.ensemble, prob.data, prob.perturbations, prob.rhat)
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    if plan.device_status() != 0:
+        raise RuntimeError("device status after warm-up: %s" % abi.fftenkf_last_error())
+
+    abi.fftenkf_set_profiling(plan.handle, True)
+    abi.fftenkf_pass_times(plan.handle)         # reset
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = str(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(gpu_id) as clk:
+        start.record(stream)
+        for _ in range(a.steps):
+            step()
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    times = abi.fftenkf_pass_times(plan.handle)
+    abi.fftenkf_set_profiling(plan.handle, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(ny) * nx * Nm * a.steps * world
+    value = units / (ms / 1e3)
+
+    # roofline of the dominant pass
+    s = 2
+    pb = pass_bytes(ny, nx, M, Nm, N_OBS, s)
+    per_pass = {}
+    for name, (tot, cnt) in times.items():
+        if cnt:
+            per_pass[name] = {"ms_per_launch": tot / cnt, "launches": cnt, "share": None}
+    total_pass_ms = sum(v["ms_per_launch"] * v["launches"] for v in per_pass.values())
+    for v in per_pass.values():
+        v["share"] = v["ms_per_launch"] * v["launches"] / total_pass_ms if total_pass_ms else None
+    dom = max((k for k in per_pass if k in pb), key=lambda k: per_pass[k]["ms_per_launch"] * per_pass[k]["launches"])
+    peak, peak_kind = hbm_peak()
+    achieved = pb[dom] / (per_pass[dom]["ms_per_launch"] / 1e3) / 1e9
+    for k, v in per_pass.items():
+        if k in pb:
+            v["alg_gbs"] = pb[k] / (v["ms_per_launch"] / 1e3) / 1e9
+            v["frac_of_peak"] = v["alg_gbs"] / peak
+    B_alg = analysis_bytes(ny, nx, M, Nm, N_OBS, s)
+    step_ms = ms / a.steps
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not a.no_e2e and a.e2e_steps > 0:
+        h_ens = prob.ensemble.cpu().pin_memory()
+        h_data = prob.data.cpu().pin_memory()
+        h_pert = prob.perturbations.cpu().pin_memory()
+        h_rhat = prob.rhat.cpu().pin_memory()
+        h_out = torch.empty_like(h_ens).pin_memory()
+        d_ens, d_data = torch.empty_like(prob.ensemble), torch.empty_like(prob.data)
+        d_pert, d_rhat = torch.empty_like(prob.perturbations), torch.empty_like(prob.rhat)
+        bi = sum(t.numel() * t.element_size() for t in (h_ens, h_data, h_pert, h_rhat))
+        bo = h_out.numel() * h_out.element_size()
+
+        def e2e_step():
+            d_ens.copy_(h_ens, non_blocking=True)
+            d_data.copy_(h_data, non_blocking=True)
+            d_pert.copy_(h_pert, non_blocking=True)
+            d_rhat.copy_(h_rhat, non_blocking=True)
+            plan.analyze(d_ens, d_data, d_pert, d_rhat)
+            h_out.copy_(d_ens, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": float(ny) * nx * Nm * a.e2e_steps * world / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": a.e2e_steps,
+               "ms_per_step": ems / a.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        n_tr = 2
+        t = oracle_sample(ny, nx, n_tr)
+        rate, transforms = oracle_rate(ny, nx, M, Nm, N_OBS, t / n_tr)
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": "%d full-size %dx%d oracle DFTs (forward + inverse, dense DFT-matrix products in FP64) "
+                         "timed in %.1f s and scaled to the %d transforms of one analysis" % (n_tr, ny, nx, t, transforms)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (bf16 storage, f64 gain)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [ny, nx], "members": Nm, "blocks": M, "observed": N_OBS,
+                       "l2": "inputs larger than L2 (2.7 GB ensemble re-read every step)",
+                       "parallelism": "independent analysis per GPU" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": kernel_traffic(dom), "alg_bytes_per_launch": pb[dom]},
+            "analysis_roofline": {"alg_bytes": B_alg, "achieved_gbs": B_alg / (step_ms / 1e3) / 1e9,
+                                  "frac": B_alg / (step_ms / 1e3) / 1e9 / peak},
+            "passes": per_pass,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "gpu_launches": 7 * a.steps,
+            "cpu_baseline": cpu,
+            "source_sha": source_sha(),
+        }
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

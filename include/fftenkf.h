@@ -1,0 +1,137 @@
+/*
+ * fftenkf.h - C ABI of the GB300 FFT Ensemble Kalman Filter analysis step.
+ *
+ * Method: Mandel, Beezley, Kondratenko, "Fast Fourier Transform Ensemble Kalman
+ * Filter with Application to a Coupled Atmosphere-Wildland Fire Model",
+ * Sec. 2.1.  Every member is transformed by the 2-D DFT F (step 1), the
+ * forecast covariance is replaced by its frequency-domain diagonal
+ *   chat_i = 1/(N-1) sum_k |uhat_ik - mean_k uhat_ik|^2              eq. (dii)
+ * with the cross spectra of eq. (cov-multi-spectral) for a block state, and the
+ * analysis is applied wavenumber by wavenumber
+ *   uhat_k^(j),a = uhat_k^(j) + chat^(jo) (chat^(oo) + rhat_o)^-1
+ *                  (dhat_o + ehat_{k,o} - uhat_k^(o))       eq. (spectral-multi-enkf)
+ * i.e. as a convolution in physical space instead of a tapered sparse solve.
+ *
+ * Conventions (all calls):
+ *  - Grids are ny x nx, doubly periodic, x fastest.  nx, ny in {2^a, 3*2^a};
+ *    16 <= nx <= 8192 and 16 <= ny <= 4096.  F is the unitary DFT, so white
+ *    noise of variance r has rhat == r (R = rI of Sec. 2.1).
+ *  - Block state of Sec. 2.1 eq. (block-enkf): M = n_blocks fields, N = n_members
+ *    members; observed_mask[j] != 0 marks H^(j) = I, all other H^(j) = 0.
+ *    Mutual cross-covariances of distinct observed blocks are neglected (the
+ *    rule Sec. 2.2 applies to the components of the morphed state): an
+ *    observed block is corrected by its own innovation only, an unobserved
+ *    block j by the sum over observed o of chat^(jo)/(chat^(oo)+rhat_o).
+ *  - The cross spectrum is chat^(jo) = 1/(N-1) sum_k ahat_k^(j) conj(ahat_k^(o)),
+ *    the frequency diagonal of the sample cross-covariance C_N^(jo).
+ *  - Half spectrum tables are [ny][nx/2+1] (k_y = 0..ny-1, k_x = 0..nx/2).
+ *  - Array arguments are DEVICE pointers owned by the caller, contiguous,
+ *    16-byte aligned (workspace: 256-byte aligned); a violation returns
+ *    FFTENKF_EINVAL before anything is launched.  Storage FFTENKF_BF16 arrays
+ *    hold bfloat16 values, FFTENKF_F32 arrays float.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *    work and return without synchronising; only fftenkf_last_device_status
+ *    waits for the stream.  Device-side failures (a non-finite covariance
+ *    estimate) are recorded in the plan's status word, never trapped.
+ *  - Calls on one plan must not overlap in time on different streams: the plan
+ *    owns one auxiliary stream and its status word.
+ */
+#ifndef FFTENKF_H
+#define FFTENKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFTENKF_OK = 0,
+  FFTENKF_EINVAL = 1,        /* bad argument: null or misaligned pointer, bad dims */
+  FFTENKF_EUNSUPPORTED = 2,  /* size not 2^a or 3*2^a in range, N < 2, too many blocks */
+  FFTENKF_ECUDA = 3,         /* a CUDA runtime call failed */
+  FFTENKF_ENONFINITE = 4,    /* non-finite spectral covariance seen on the device */
+  FFTENKF_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+  FFTENKF_ENOMEM = 6         /* device allocation failed */
+} fftenkf_status;
+
+typedef enum { FFTENKF_F32 = 0, FFTENKF_BF16 = 1 } fftenkf_storage;
+
+typedef struct {
+  int ny, nx;        /* grid */
+  int n_blocks;      /* M, 1..16 */
+  int n_members;     /* N >= 2 (eq. dii divides by N-1) */
+  int storage;       /* fftenkf_storage of ensemble and perturbations */
+} fftenkf_dims;
+
+typedef struct fftenkf_plan_s* fftenkf_plan;
+
+/* Create a plan for one (dims, observed_mask).  observed_mask: HOST array of
+ * n_blocks bytes.  The plan owns twiddle tables, a device status word and an
+ * auxiliary stream; it allocates device memory (a few MB) here only.
+ * Returns EUNSUPPORTED when the sizes or block counts are outside the limits
+ * above or the per-wavenumber statistics do not fit in shared memory. */
+fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_dims* dims,
+                                   const uint8_t* observed_mask);
+fftenkf_status fftenkf_plan_destroy(fftenkf_plan plan);
+
+/* Bytes of device workspace estimate_spectrum / analyze need. */
+fftenkf_status fftenkf_workspace_size(fftenkf_plan plan, size_t* bytes);
+
+/* Number of doubles in a spectrum table set: n_obs*K real auto tables followed
+ * by n_obs*n_unobs complex cross tables (2K doubles each), K = ny*(nx/2+1).
+ * Order: chat^(oo) for observed o ascending; then for observed o ascending,
+ * chat^(jo) for unobserved j ascending; complex values as (re, im) pairs. */
+fftenkf_status fftenkf_spectrum_size(fftenkf_plan plan, size_t* n_doubles);
+
+/* Steps 1-2 of Sec. 2.1 (eq. dii, eq. cov-multi-spectral): the spectral
+ * covariance tables of `ensemble` ([M][N][ny][nx], storage dtype), unitary
+ * scaling, written to spectrum_out (device, fftenkf_spectrum_size doubles).
+ * workspace: device buffer of fftenkf_workspace_size bytes, or NULL to use a
+ * buffer the plan allocates on first use and keeps. */
+fftenkf_status fftenkf_estimate_spectrum(fftenkf_plan plan, const void* ensemble, double* spectrum_out,
+                                         void* workspace, void* stream);
+
+/* The analysis of eq. (spectral-multi-enkf), in place on `ensemble`
+ * ([M][N][ny][nx], storage dtype; rounded to nearest even for BF16).
+ *   data          [n_obs][ny][nx] float: d for every observed block (ascending)
+ *   perturbations [N][n_obs][ny][nx] storage dtype: e_k ~ N(0, R) (Sec. 2)
+ *   rhat          [n_obs][ny][nx/2+1] double: spectral data-error variance; it
+ *                 must be even in k (rhat(-k) = rhat(k)), as the spectrum of a
+ *                 real noise field is; where chat^(oo) + rhat == 0 the gain is 0
+ *   spectrum      NULL: estimated from the ensemble (steps 1-2); otherwise a
+ *                 caller-supplied table set in the fftenkf_spectrum_size layout
+ *                 (e.g. a denoised or exact spectrum) used in place of chat.
+ * The result is u + Re F^-1[...]; with a caller spectrum that is not
+ * Hermitian-symmetric on the k_x = 0 and k_x = nx/2 columns the real part is
+ * what is returned. */
+fftenkf_status fftenkf_analyze(fftenkf_plan plan, void* ensemble, const float* data,
+                               const void* perturbations, const double* rhat, const double* spectrum,
+                               void* workspace, void* stream);
+
+/* Wait for `stream`, then return and clear the plan's device status word:
+ * FFTENKF_OK, FFTENKF_ENONFINITE, or FFTENKF_ECUDA if the stream reported an
+ * error. */
+fftenkf_status fftenkf_last_device_status(fftenkf_plan plan, void* stream);
+
+/* Per-pass timing (tracing).  With profiling enabled every pass of the calls
+ * on this plan is bracketed by CUDA events on the stream it runs on.
+ * fftenkf_pass_times waits for those events, writes for every pass p <
+ * n_passes its total device milliseconds and number of launches since the
+ * last read (or enable), and resets the totals.  Passes are numbered
+ * 0..fftenkf_pass_count()-1 and named by fftenkf_pass_name. */
+fftenkf_status fftenkf_set_profiling(fftenkf_plan plan, int enable);
+fftenkf_status fftenkf_pass_times(fftenkf_plan plan, double* total_ms, int* launches, int n_passes);
+int fftenkf_pass_count(void);
+const char* fftenkf_pass_name(int pass);
+
+/* Static description of a status code. */
+const char* fftenkf_status_string(fftenkf_status s);
+/* Message of the last failing call on this host thread ("" if none). */
+const char* fftenkf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTENKF_H */

@@ -1,0 +1,156 @@
+"""ctypes binding of the C ABI in include/fftenkf.h: same names, argument marshalling only.
+
+Every function here forwards to the shared library built from csrc/; nothing is
+computed in Python.  Import fails loudly if the library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfftenkf.so")
+
+FFTENKF_OK = 0
+FFTENKF_EINVAL = 1
+FFTENKF_EUNSUPPORTED = 2
+FFTENKF_ECUDA = 3
+FFTENKF_ENONFINITE = 4
+FFTENKF_ETIMEOUT = 5
+FFTENKF_ENOMEM = 6
+FFTENKF_F32 = 0
+FFTENKF_BF16 = 1
+
+
+class fftenkf_dims(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("n_blocks", ctypes.c_int),
+                ("n_members", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+class FftEnkfError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__("%s: %s (%s)" % (where, fftenkf_status_string(status), message))
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGNATURES = [
+    ("fftenkf_plan_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fftenkf_dims), ctypes.c_char_p]),
+    ("fftenkf_plan_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("fftenkf_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("fftenkf_spectrum_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("fftenkf_estimate_spectrum", ctypes.c_int, [ctypes.c_void_p] * 5),
+    ("fftenkf_analyze", ctypes.c_int, [ctypes.c_void_p] * 8),
+    ("fftenkf_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fftenkf_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("fftenkf_pass_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("fftenkf_pass_count", ctypes.c_int, []),
+    ("fftenkf_pass_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("fftenkf_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("fftenkf_last_error", ctypes.c_char_p, []),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfftenkf.so not built; run `python -m paper_1001_1588_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names of the entry points the binding knows about."""
+    return [s[0] for s in _SIGNATURES]
+
+
+def fftenkf_status_string(status: int) -> str:
+    return lib().fftenkf_status_string(status).decode()
+
+
+def fftenkf_last_error() -> str:
+    return lib().fftenkf_last_error().decode()
+
+
+def check(status: int, where: str) -> None:
+    if status != FFTENKF_OK:
+        raise FftEnkfError(status, where, fftenkf_last_error())
+
+
+def _p(x):
+    """Pointer argument: None, int address, or an object with data_ptr()."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def fftenkf_plan_create(ny, nx, n_blocks, n_members, storage, observed_mask):
+    d = fftenkf_dims(ny, nx, n_blocks, n_members, storage)
+    plan = ctypes.c_void_p()
+    mask = bytes(int(bool(m)) for m in observed_mask)
+    check(lib().fftenkf_plan_create(ctypes.byref(plan), ctypes.byref(d), mask), "fftenkf_plan_create")
+    return plan.value
+
+
+def fftenkf_plan_destroy(plan):
+    check(lib().fftenkf_plan_destroy(plan), "fftenkf_plan_destroy")
+
+
+def fftenkf_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    check(lib().fftenkf_workspace_size(plan, ctypes.byref(n)), "fftenkf_workspace_size")
+    return n.value
+
+
+def fftenkf_spectrum_size(plan) -> int:
+    n = ctypes.c_size_t()
+    check(lib().fftenkf_spectrum_size(plan, ctypes.byref(n)), "fftenkf_spectrum_size")
+    return n.value
+
+
+def fftenkf_estimate_spectrum(plan, ensemble, spectrum_out, workspace=None, stream=None):
+    check(lib().fftenkf_estimate_spectrum(plan, _p(ensemble), _p(spectrum_out), _p(workspace), stream),
+          "fftenkf_estimate_spectrum")
+
+
+def fftenkf_analyze(plan, ensemble, data, perturbations, rhat, spectrum=None, workspace=None, stream=None):
+    check(lib().fftenkf_analyze(plan, _p(ensemble), _p(data), _p(perturbations), _p(rhat), _p(spectrum),
+                                _p(workspace), stream), "fftenkf_analyze")
+
+
+def fftenkf_last_device_status(plan, stream=None) -> int:
+    return lib().fftenkf_last_device_status(plan, stream)
+
+
+def fftenkf_set_profiling(plan, enable: bool):
+    check(lib().fftenkf_set_profiling(plan, int(bool(enable))), "fftenkf_set_profiling")
+
+
+def fftenkf_pass_count() -> int:
+    return lib().fftenkf_pass_count()
+
+
+def fftenkf_pass_name(i: int) -> str:
+    return lib().fftenkf_pass_name(i).decode()
+
+
+def fftenkf_pass_times(plan):
+    """{pass name: (total ms, launches)} since the last read; waits for the events."""
+    n = fftenkf_pass_count()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    check(lib().fftenkf_pass_times(plan, ms, cnt, n), "fftenkf_pass_times")
+    return {fftenkf_pass_name(i): (ms[i], cnt[i]) for i in range(n)}

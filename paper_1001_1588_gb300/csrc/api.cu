@@ -1,0 +1,416 @@
+// C ABI: plans, argument validation and the order of the passes.
+//
+// analyze (Sec. 2.1, eq. spectral-multi-enkf), on the caller's stream unless noted:
+//   1. mean            ubar^(j) over members                          (eq. dii)
+//   2. row_fwd anomaly  rows of F(u_k^(j) - ubar^(j)) -> A
+//   3. col_stats       columns of F, chat^(oo), chat^(jo) -> chat_t   (eq. dii, cov-multi-spectral)
+//   4. gain            FP64 gains -> goo, gjo          [auxiliary stream, overlaps 5]
+//   5. row_fwd innov   rows of F(d_o + e_{k,o} - u_k^(o)) -> W
+//   6. col_update      gain x innovation, inverse columns -> S (aliases A)
+//   7. row_inv         inverse rows, u_k^(j) += increment
+// With a caller-supplied spectrum, 1-3 are skipped and 4 reads the tables.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fftenkf.h"
+#include "common.cuh"
+
+using namespace fftenkf;
+
+enum Pass { kPassMean, kPassRowAnom, kPassStats, kPassGain, kPassRowInnov, kPassUpdate, kPassRowInv,
+            kPassChatOut, kPassCount };
+static const char* kPassNames[kPassCount] = {"mean", "row_fwd_anomaly", "col_stats", "gain",
+                                             "row_fwd_innovation", "col_update", "row_inv", "chat_out"};
+
+namespace {
+thread_local std::string g_last_error;
+
+fftenkf_status fail(fftenkf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+fftenkf_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(FFTENKF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+bool is_line(int n) { return line_supported(n); }
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+}  // namespace
+
+struct fftenkf_plan_s {
+  int ny, nx, L, M, N, storage;
+  int n_obs, n_un;
+  int obs[kMaxObs];
+  int un[kMaxBlocks];
+  int obs_of_block[kMaxBlocks];
+  int un_of_block[kMaxBlocks];
+  float2* d_tw = nullptr;     // [L] row twiddles, [ny] column twiddles, [L+1] real-FFT twiddles
+  int* d_status = nullptr;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // workspace layout (byte offsets)
+  size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, ws_bytes;
+  void* own_ws = nullptr;
+  int device = 0;
+  // per-pass CUDA-event timing (fftenkf_set_profiling); a ring of event pairs per pass
+  bool prof = false;
+  static constexpr int kSlots = 64;
+  cudaEvent_t ev[kPassCount][kSlots][2] = {};
+  int used[kPassCount] = {};
+  double acc_ms[kPassCount] = {};
+  int launches[kPassCount] = {};
+  const float2* twL() const { return d_tw; }
+  const float2* twY() const { return d_tw + L; }
+  const float2* twX() const { return d_tw + L + ny; }
+};
+
+// fold a completed slot into the totals
+static void prof_drain(fftenkf_plan p, int pass, int slot) {
+  float ms = 0.f;
+  cudaEventSynchronize(p->ev[pass][slot][1]);
+  if (cudaEventElapsedTime(&ms, p->ev[pass][slot][0], p->ev[pass][slot][1]) == cudaSuccess) {
+    p->acc_ms[pass] += ms;
+    p->launches[pass] += 1;
+  }
+}
+static void prof_begin(fftenkf_plan p, int pass, cudaStream_t s) {
+  if (!p->prof) return;
+  int slot = p->used[pass] % fftenkf_plan_s::kSlots;
+  if (p->used[pass] >= fftenkf_plan_s::kSlots) prof_drain(p, pass, slot);
+  if (!p->ev[pass][slot][0]) {
+    cudaEventCreate(&p->ev[pass][slot][0]);
+    cudaEventCreate(&p->ev[pass][slot][1]);
+  }
+  cudaEventRecord(p->ev[pass][slot][0], s);
+}
+static void prof_end(fftenkf_plan p, int pass, cudaStream_t s) {
+  if (!p->prof) return;
+  int slot = p->used[pass] % fftenkf_plan_s::kSlots;
+  cudaEventRecord(p->ev[pass][slot][1], s);
+  p->used[pass] += 1;
+}
+
+static void host_twiddles(std::vector<float2>& out, int n, int count) {
+  for (int e = 0; e < count; ++e) {
+    const long long r = e % n;
+    const double ang = 2.0 * M_PI * (double)r / (double)n;
+    out.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
+  }
+}
+
+extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_dims* dims,
+                                              const uint8_t* observed_mask) {
+  g_last_error.clear();
+  if (!plan || !dims || !observed_mask) return fail(FFTENKF_EINVAL, "null argument");
+  *plan = nullptr;
+  const fftenkf_dims d = *dims;
+  if (d.ny <= 0 || d.nx <= 0 || d.n_blocks <= 0 || d.n_members <= 0)
+    return fail(FFTENKF_EINVAL, "dimensions must be positive");
+  if (d.storage != FFTENKF_F32 && d.storage != FFTENKF_BF16) return fail(FFTENKF_EINVAL, "unknown storage");
+  if (d.n_members < 2) return fail(FFTENKF_EUNSUPPORTED, "need at least 2 members (eq. dii divides by N-1)");
+  if (d.n_blocks > kMaxBlocks) return fail(FFTENKF_EUNSUPPORTED, "at most 16 blocks");
+  if (d.nx % 2 || !row_line_supported(d.nx / 2) || d.nx < 16 || d.nx > 8192)
+    return fail(FFTENKF_EUNSUPPORTED, "nx must be 2^a or 3*2^a in [16, 8192]");
+  if (!is_line(d.ny) || d.ny < 16 || d.ny > 4096)
+    return fail(FFTENKF_EUNSUPPORTED, "ny must be 2^a or 3*2^a in [16, 4096]");
+  fftenkf_plan_s* p = new fftenkf_plan_s();
+  p->ny = d.ny;
+  p->nx = d.nx;
+  p->L = d.nx / 2;
+  p->M = d.n_blocks;
+  p->N = d.n_members;
+  p->storage = d.storage;
+  p->n_obs = p->n_un = 0;
+  for (int j = 0; j < p->M; ++j) {
+    p->obs_of_block[j] = p->un_of_block[j] = -1;
+    if (observed_mask[j]) {
+      if (p->n_obs >= kMaxObs) {
+        delete p;
+        return fail(FFTENKF_EUNSUPPORTED, "at most 4 observed blocks");
+      }
+      p->obs_of_block[j] = p->n_obs;
+      p->obs[p->n_obs++] = j;
+    } else {
+      p->un_of_block[j] = p->n_un;
+      p->un[p->n_un++] = j;
+    }
+  }
+  const int nf = p->n_obs + 2 * p->n_obs * p->n_un;
+  if (p->n_obs > 0 && col_stats_smem(p->ny, nf, nullptr) == 0) {
+    delete p;
+    return fail(FFTENKF_EUNSUPPORTED, "covariance tables per column exceed shared memory (reduce blocks or ny)");
+  }
+  // workspace layout
+  const size_t G = (size_t)p->ny * p->nx;
+  const size_t line = (size_t)p->L * p->ny * sizeof(float2);     // one field's row spectra
+  const size_t tab = (size_t)(p->L + 1) * p->ny;
+  size_t off = 0;
+  p->off_mean = off; off = round_up(off + (size_t)p->M * G * sizeof(float), 256);
+  p->off_A = off;    off = round_up(off + (size_t)p->M * p->N * line, 256);
+  p->off_chat = off; off = round_up(off + (size_t)nf * tab * sizeof(float), 256);
+  p->off_W = off;    off = round_up(off + (size_t)p->N * p->n_obs * line, 256);
+  p->off_goo = off;  off = round_up(off + (size_t)p->n_obs * tab * sizeof(float), 256);
+  p->off_gjo = off;  off = round_up(off + (size_t)p->n_obs * p->n_un * tab * sizeof(float2), 256);
+  p->ws_bytes = off;
+  cudaGetDevice(&p->device);
+  std::vector<float2> tw;
+  host_twiddles(tw, p->L, p->L);
+  host_twiddles(tw, p->ny, p->ny);
+  host_twiddles(tw, p->nx, p->L + 1);
+  cudaError_t e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(FFTENKF_ENOMEM, "twiddle allocation failed");
+  }
+  e = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fftenkf_plan_destroy(p);
+    return cuda_fail(e, "plan_create");
+  }
+  *plan = p;
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_plan_destroy(fftenkf_plan p) {
+  if (!p) return FFTENKF_OK;
+  if (p->own_ws) cudaFree(p->own_ws);
+  if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_status) cudaFree(p->d_status);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->aux) cudaStreamDestroy(p->aux);
+  for (int a = 0; a < kPassCount; ++a)
+    for (int b = 0; b < fftenkf_plan_s::kSlots; ++b)
+      for (int c = 0; c < 2; ++c)
+        if (p->ev[a][b][c]) cudaEventDestroy(p->ev[a][b][c]);
+  delete p;
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_workspace_size(fftenkf_plan p, size_t* bytes) {
+  if (!p || !bytes) return fail(FFTENKF_EINVAL, "null argument");
+  *bytes = p->ws_bytes;
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_spectrum_size(fftenkf_plan p, size_t* n) {
+  if (!p || !n) return fail(FFTENKF_EINVAL, "null argument");
+  const size_t K = (size_t)p->ny * (p->L + 1);
+  *n = (size_t)p->n_obs * K + (size_t)p->n_obs * p->n_un * 2 * K;
+  return FFTENKF_OK;
+}
+
+static fftenkf_status get_workspace(fftenkf_plan p, void* ws, char** out) {
+  if (ws) {
+    if (!aligned(ws, 256)) return fail(FFTENKF_EINVAL, "workspace must be 256-byte aligned");
+    *out = static_cast<char*>(ws);
+    return FFTENKF_OK;
+  }
+  if (!p->own_ws) {
+    cudaError_t e = cudaMalloc(&p->own_ws, p->ws_bytes);
+    if (e != cudaSuccess) {
+      p->own_ws = nullptr;
+      return fail(FFTENKF_ENOMEM, "workspace allocation failed");
+    }
+  }
+  *out = static_cast<char*>(p->own_ws);
+  return FFTENKF_OK;
+}
+
+// steps 1-3: mean, anomaly row spectra, column statistics -> chat_t
+static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s) {
+  MeanParams mp;
+  mp.M = p->M;
+  mp.N = p->N;
+  mp.storage = p->storage;
+  mp.G = (long long)p->ny * p->nx;
+  mp.ens = ens;
+  mp.mean = reinterpret_cast<float*>(ws + p->off_mean);
+  prof_begin(p, kPassMean, s);
+  cudaError_t e = launch_mean(mp, s);
+  prof_end(p, kPassMean, s);
+  if (e != cudaSuccess) return e;
+  RowFwdParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
+  rp.n_obs = p->n_obs; rp.mode = kAnomaly; rp.storage = p->storage;
+  rp.ens = ens; rp.mean = mp.mean;
+  rp.out = reinterpret_cast<float2*>(ws + p->off_A);
+  rp.twL = p->twL(); rp.twX = p->twX();
+  prof_begin(p, kPassRowAnom, s);
+  e = launch_row_fwd(rp, p->M * p->N, s);
+  prof_end(p, kPassRowAnom, s);
+  if (e != cudaSuccess) return e;
+  ColStatsParams cp;
+  memset(&cp, 0, sizeof(cp));
+  cp.ny = p->ny; cp.L = p->L; cp.M = p->M; cp.N = p->N; cp.n_obs = p->n_obs; cp.n_un = p->n_un;
+  for (int i = 0; i < p->n_obs; ++i) cp.obs[i] = p->obs[i];
+  for (int u = 0; u < p->n_un; ++u) cp.un[u] = p->un[u];
+  cp.A = rp.out;
+  cp.chat = reinterpret_cast<float*>(ws + p->off_chat);
+  cp.scale = (float)(1.0 / ((double)(p->N - 1) * (double)p->ny * (double)p->nx));
+  cp.twY = p->twY();
+  cp.status = p->d_status;
+  prof_begin(p, kPassStats, s);
+  e = launch_col_stats(cp, s);
+  prof_end(p, kPassStats, s);
+  return e;
+}
+
+extern "C" fftenkf_status fftenkf_estimate_spectrum(fftenkf_plan p, const void* ensemble, double* spectrum_out,
+                                                    void* workspace, void* stream) {
+  g_last_error.clear();
+  if (!p || !ensemble || !spectrum_out) return fail(FFTENKF_EINVAL, "null argument");
+  if (!aligned(ensemble, 16) || !aligned(spectrum_out, 16)) return fail(FFTENKF_EINVAL, "pointers must be 16-byte aligned");
+  if (p->n_obs == 0) return FFTENKF_OK;   // no tables
+  char* ws;
+  fftenkf_status st = get_workspace(p, workspace, &ws);
+  if (st != FFTENKF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = run_statistics(p, ensemble, ws, s);
+  prof_begin(p, kPassChatOut, s);
+  if (e == cudaSuccess)
+    e = launch_chat_out(reinterpret_cast<float*>(ws + p->off_chat), spectrum_out, p->ny, p->L, p->n_obs, p->n_un, s);
+  prof_end(p, kPassChatOut, s);
+  if (e != cudaSuccess) return cuda_fail(e, "estimate_spectrum");
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const float* data, const void* perturbations,
+                                          const double* rhat, const double* spectrum, void* workspace, void* stream) {
+  g_last_error.clear();
+  if (!p || !ensemble) return fail(FFTENKF_EINVAL, "null argument");
+  if (p->n_obs == 0) return FFTENKF_OK;   // nothing observed: the forecast is the analysis
+  if (!data || !perturbations || !rhat) return fail(FFTENKF_EINVAL, "null argument");
+  if (!aligned(ensemble, 16) || !aligned(data, 16) || !aligned(perturbations, 16) || !aligned(rhat, 16) ||
+      (spectrum && !aligned(spectrum, 16)))
+    return fail(FFTENKF_EINVAL, "pointers must be 16-byte aligned");
+  char* ws;
+  fftenkf_status st = get_workspace(p, workspace, &ws);
+  if (st != FFTENKF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!spectrum) e = run_statistics(p, ensemble, ws, s);
+  // gains on the auxiliary stream, overlapping the innovation row pass
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
+  GainParams gp;
+  memset(&gp, 0, sizeof(gp));
+  gp.ny = p->ny; gp.L = p->L; gp.n_obs = p->n_obs; gp.n_un = p->n_un;
+  gp.chat_t = spectrum ? nullptr : reinterpret_cast<const float*>(ws + p->off_chat);
+  gp.spec = spectrum;
+  gp.rhat = rhat;
+  gp.goo = reinterpret_cast<float*>(ws + p->off_goo);
+  gp.gjo = reinterpret_cast<float2*>(ws + p->off_gjo);
+  gp.scale = (float)(1.0 / ((double)p->ny * (double)p->nx));
+  gp.status = p->d_status;
+  prof_begin(p, kPassGain, p->aux);
+  if (e == cudaSuccess) e = launch_gain(gp, p->aux);
+  prof_end(p, kPassGain, p->aux);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
+  RowFwdParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
+  rp.n_obs = p->n_obs; rp.mode = kInnovation; rp.storage = p->storage;
+  for (int i = 0; i < p->n_obs; ++i) rp.obs[i] = p->obs[i];
+  rp.ens = ensemble; rp.data = data; rp.pert = perturbations;
+  rp.out = reinterpret_cast<float2*>(ws + p->off_W);
+  rp.twL = p->twL(); rp.twX = p->twX();
+  prof_begin(p, kPassRowInnov, s);
+  if (e == cudaSuccess) e = launch_row_fwd(rp, p->N * p->n_obs, s);
+  prof_end(p, kPassRowInnov, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+  ColUpdParams up;
+  memset(&up, 0, sizeof(up));
+  up.ny = p->ny; up.L = p->L; up.M = p->M; up.N = p->N; up.n_obs = p->n_obs; up.n_un = p->n_un;
+  for (int j = 0; j < p->M; ++j) {
+    up.obs_of_block[j] = p->obs_of_block[j];
+    up.un_of_block[j] = p->un_of_block[j];
+  }
+  up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
+  up.S = reinterpret_cast<float2*>(ws + p->off_A);
+  up.twY = p->twY();
+  prof_begin(p, kPassUpdate, s);
+  if (e == cudaSuccess) e = launch_col_update(up, s);
+  prof_end(p, kPassUpdate, s);
+  RowInvParams ip;
+  memset(&ip, 0, sizeof(ip));
+  ip.ny = p->ny; ip.nx = p->nx; ip.L = p->L; ip.M = p->M; ip.N = p->N; ip.storage = p->storage;
+  ip.in = up.S; ip.ens = ensemble; ip.twL = p->twL(); ip.twX = p->twX();
+  prof_begin(p, kPassRowInv, s);
+  if (e == cudaSuccess) e = launch_row_inv(ip, p->M * p->N, s);
+  prof_end(p, kPassRowInv, s);
+  if (e != cudaSuccess) return cuda_fail(e, "analyze");
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_last_device_status(fftenkf_plan p, void* stream) {
+  if (!p) return fail(FFTENKF_EINVAL, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  int word = 0;
+  e = cudaMemcpy(&word, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "status word");
+  if (word & kStatusNonFinite) return fail(FFTENKF_ENONFINITE, "non-finite spectral covariance");
+  return FFTENKF_OK;
+}
+
+extern "C" const char* fftenkf_status_string(fftenkf_status s) {
+  switch (s) {
+    case FFTENKF_OK: return "ok";
+    case FFTENKF_EINVAL: return "invalid argument";
+    case FFTENKF_EUNSUPPORTED: return "unsupported size or configuration";
+    case FFTENKF_ECUDA: return "CUDA error";
+    case FFTENKF_ENONFINITE: return "non-finite spectral covariance";
+    case FFTENKF_ETIMEOUT: return "device wait timed out";
+    case FFTENKF_ENOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* fftenkf_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" fftenkf_status fftenkf_set_profiling(fftenkf_plan p, int enable) {
+  if (!p) return fail(FFTENKF_EINVAL, "null argument");
+  p->prof = enable != 0;
+  for (int a = 0; a < kPassCount; ++a) {
+    p->used[a] = 0;
+    p->acc_ms[a] = 0.0;
+    p->launches[a] = 0;
+  }
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_pass_times(fftenkf_plan p, double* total_ms, int* launches, int n_passes) {
+  if (!p || !total_ms || !launches) return fail(FFTENKF_EINVAL, "null argument");
+  for (int a = 0; a < kPassCount; ++a) {
+    const int n = p->used[a] < fftenkf_plan_s::kSlots ? p->used[a] : fftenkf_plan_s::kSlots;
+    const int first = p->used[a] < fftenkf_plan_s::kSlots ? 0 : p->used[a] % fftenkf_plan_s::kSlots;
+    for (int i = 0; i < n; ++i) prof_drain(p, a, (first + i) % fftenkf_plan_s::kSlots);
+    if (a < n_passes) {
+      total_ms[a] = p->acc_ms[a];
+      launches[a] = p->launches[a];
+    }
+    p->used[a] = 0;
+    p->acc_ms[a] = 0.0;
+    p->launches[a] = 0;
+  }
+  return FFTENKF_OK;
+}
+
+extern "C" int fftenkf_pass_count(void) { return kPassCount; }
+
+extern "C" const char* fftenkf_pass_name(int pass) {
+  return (pass >= 0 && pass < kPassCount) ? kPassNames[pass] : "";
+}

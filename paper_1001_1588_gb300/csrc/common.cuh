@@ -1,0 +1,125 @@
+// Shared definitions of the analysis kernels: launch parameters, layouts and
+// element access for the two storage types.
+//
+// Spectral intermediates ("row spectra") are stored per field as
+// [nx/2][ny] float2: for every packed row-spectrum column c the ny values are
+// contiguous, so the column passes read and write whole lines with unit
+// stride.  Packed column 0 carries the real DC value of each row in .x and the
+// real Nyquist value in .y (both are real for a real row).  The column passes
+// treat k_x = 0 and k_x = nx/2 as "virtual columns" 0 and nx/2 that take the
+// .x or the .y part of packed column 0, so every wavenumber column k_x in
+// [0, nx/2] is one line of length ny.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+
+namespace fftenkf {
+
+constexpr int kMaxBlocks = 16;
+constexpr int kMaxObs = 4;
+
+enum RowMode { kAnomaly = 0, kInnovation = 1 };
+enum Storage { kF32 = 0, kBF16 = 1 };
+
+// Status bits written by kernels (OR-ed into the plan's device word).
+enum DeviceStatusBits { kStatusNonFinite = 1 };
+
+__device__ __forceinline__ float2 load2(const void* base, size_t idx, int storage) {
+  // two consecutive elements idx, idx+1 (idx even)
+  if (storage == kBF16) {
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(
+        reinterpret_cast<const __nv_bfloat16*>(base) + idx);
+    return __bfloat1622float2(b);
+  }
+  return *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base) + idx);
+}
+
+__device__ __forceinline__ void store2(void* base, size_t idx, float2 v, int storage) {
+  if (storage == kBF16) {
+    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base) + idx) =
+        __float22bfloat162_rn(v);
+  } else {
+    *reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + idx) = v;
+  }
+}
+
+struct MeanParams {
+  int M, N, storage;
+  long long G;            // grid points per field
+  const void* ens;        // [M][N][G]
+  float* mean;            // [M][G]
+};
+
+struct RowFwdParams {
+  int ny, nx, L, R;       // L = nx/2, R rows per CTA
+  int M, N, n_obs, mode, storage;
+  int n_tiles;            // ny / R
+  int obs[kMaxObs];
+  const void* ens;        // [M][N][ny][nx]
+  const float* mean;      // [M][ny][nx]         (anomaly mode)
+  const float* data;      // [n_obs][ny][nx]     (innovation mode)
+  const void* pert;       // [N][n_obs][ny][nx]  (innovation mode)
+  float2* out;            // row spectra: anomaly field j*N+k, innovation field k*n_obs+i
+  const float2* twL;      // exp(-2 pi i e / L), e < L
+  const float2* twX;      // exp(-2 pi i k / nx), k <= L
+};
+
+struct RowInvParams {
+  int ny, nx, L, R, M, N, storage, n_tiles;
+  const float2* in;       // row spectra of the increments, field j*N+k
+  void* ens;              // [M][N][ny][nx], updated in place
+  const float2* twL;
+  const float2* twX;
+};
+
+struct ColStatsParams {
+  int ny, L, M, N, n_obs, n_un;
+  int obs[kMaxObs];
+  int un[kMaxBlocks];
+  const float2* A;        // anomaly row spectra, field j*N+k
+  float* chat;            // [n_obs][L+1][ny] real, then [n_obs*n_un][L+1][ny] float2
+  float scale;            // 1 / ((N-1) * ny * nx)
+  const float2* twY;      // exp(-2 pi i e / ny)
+  int* status;
+};
+
+struct ColUpdParams {
+  int ny, L, M, N, n_obs, n_un;
+  int obs_of_block[kMaxBlocks];   // observed index of block j, or -1
+  int un_of_block[kMaxBlocks];    // unobserved index of block j, or -1
+  const float2* W;        // innovation row spectra, field k*n_obs+i
+  const float* goo;       // [n_obs][L+1][ny]
+  const float2* gjo;      // [n_obs*n_un][L+1][ny], table i*n_un+u
+  float2* S;              // increment row spectra, field j*N+k
+  const float2* twY;
+};
+
+struct GainParams {
+  int ny, L, n_obs, n_un;
+  const float* chat_t;    // stats kernel output (transposed, float), or null
+  const double* spec;     // caller spectrum (natural layout, double), or null
+  const double* rhat;     // [n_obs][ny][L+1]
+  float* goo;
+  float2* gjo;
+  float scale;            // 1 / (ny*nx): folds the unnormalised inverse transform
+  int* status;
+};
+
+// host-side launchers (one switch over the line length per pass)
+cudaError_t launch_mean(const MeanParams& p, cudaStream_t s);
+cudaError_t launch_row_fwd(const RowFwdParams& p, int n_fields, cudaStream_t s);
+cudaError_t launch_row_inv(const RowInvParams& p, int n_fields, cudaStream_t s);
+cudaError_t launch_col_stats(const ColStatsParams& p, cudaStream_t s);
+cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s);
+cudaError_t launch_gain(const GainParams& p, cudaStream_t s);
+cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, int n_obs, int n_un,
+                            cudaStream_t s);
+bool line_supported(int n);       // column line lengths
+bool row_line_supported(int n);   // row line lengths (nx/2)
+// shared-memory bytes a pass needs (0 = unsupported), for plan-time checks
+size_t col_stats_smem(int ny, int nf, int* lpc);
+
+}  // namespace fftenkf

@@ -1,0 +1,237 @@
+// Register/shared-memory FFT of one line, the building block of every pass.
+//
+// A line of N complex values (N = 2^a or 3*2^a) is transformed by T = N/V
+// threads.  Data is held in the "canonical" distribution: thread t owns
+// elements t + T*m in register slot m (m < V), both on input and on output,
+// so a line is loaded from and stored to global memory with unit-stride,
+// fully coalesced warp accesses, and a forward transform's output can feed an
+// inverse transform without any exchange.  Between radix stages the values go
+// through a padded shared-memory line buffer (Stockham self-sorting order), so
+// no bit reversal is needed.  Radices are 16, 8, 4, 2 and 3; the plan is fixed
+// at compile time from (N, V).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftenkf {
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward sign) or +i (inverse sign)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ------------------------------------------------------------------ plan
+__host__ __device__ constexpr int pick_radix(int rem, int V) {
+  return (rem % 16 == 0 && V % 16 == 0) ? 16
+       : (rem % 8 == 0 && V % 8 == 0)   ? 8
+       : (rem % 4 == 0 && V % 4 == 0)   ? 4
+       : (rem % 2 == 0 && V % 2 == 0)   ? 2
+       : (rem % 3 == 0 && V % 3 == 0)   ? 3
+                                        : 0;
+}
+__host__ __device__ constexpr int radix_at(int N, int V, int s) {
+  int rem = N;
+  for (int i = 0; i < s; ++i) rem /= pick_radix(rem, V);
+  return rem == 1 ? 1 : pick_radix(rem, V);
+}
+__host__ __device__ constexpr int num_stages(int N, int V) {
+  int rem = N, s = 0;
+  while (rem > 1) {
+    int r = pick_radix(rem, V);
+    if (r == 0) return -1;
+    rem /= r;
+    ++s;
+  }
+  return s;
+}
+// default values per thread: 16 for powers of two, 24 (or N) for 3*2^a
+__host__ __device__ constexpr int default_V(int N) {
+  return (N % 3 == 0) ? (N >= 24 ? 24 : N) : (N >= 16 ? 16 : N);
+}
+// padded shared-memory index: one spare slot per 16 keeps stride-R writes
+// of the Stockham stages on distinct 8-byte banks
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
+
+// ------------------------------------------------------------------ small DFTs
+// Forward kernels use exp(-2 pi i / R); INV uses exp(+2 pi i / R).
+template <int R, bool INV> struct Dft;
+
+template <bool INV> struct Dft<2, INV> {
+  static __device__ __forceinline__ void run(float2* a) {
+    float2 t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  }
+};
+
+template <bool INV> struct Dft<3, INV> {
+  static __device__ __forceinline__ void run(float2* a) {
+    const float h = 0.86602540378443864676f;  // sin(2 pi / 3)
+    float2 s = cadd(a[1], a[2]);
+    float2 d = cscale(csub(a[1], a[2]), h);
+    float2 m = make_float2(a[0].x - 0.5f * s.x, a[0].y - 0.5f * s.y);
+    a[0] = cadd(a[0], s);
+    float2 rd = rot90<INV>(d);       // -i d (forward)
+    a[1] = cadd(m, rd);
+    a[2] = csub(m, rd);
+  }
+};
+
+template <bool INV> struct Dft<4, INV> {
+  static __device__ __forceinline__ void run(float2* a) {
+    float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+    float2 t2 = cadd(a[1], a[3]), t3 = rot90<INV>(csub(a[1], a[3]));
+    a[0] = cadd(t0, t2);
+    a[2] = csub(t0, t2);
+    a[1] = cadd(t1, t3);
+    a[3] = csub(t1, t3);
+  }
+};
+
+// multiply by exp(-+ 2 pi i e / 8) for e = 1, 2, 3
+template <int E, bool INV>
+__device__ __forceinline__ float2 w8(float2 v) {
+  const float c = 0.70710678118654752440f;
+  if (E == 0) return v;
+  if (E == 2) return rot90<INV>(v);
+  if (E == 1) return INV ? make_float2(c * (v.x - v.y), c * (v.x + v.y))
+                         : make_float2(c * (v.x + v.y), c * (v.y - v.x));
+  // E == 3
+  return INV ? make_float2(-c * (v.x + v.y), c * (v.x - v.y))
+             : make_float2(c * (v.y - v.x), -c * (v.x + v.y));
+}
+
+template <bool INV> struct Dft<8, INV> {
+  static __device__ __forceinline__ void run(float2* a) {
+    float2 e[4] = {a[0], a[2], a[4], a[6]};
+    float2 o[4] = {a[1], a[3], a[5], a[7]};
+    Dft<4, INV>::run(e);
+    Dft<4, INV>::run(o);
+    o[1] = w8<1, INV>(o[1]);
+    o[2] = w8<2, INV>(o[2]);
+    o[3] = w8<3, INV>(o[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = cadd(e[k], o[k]);
+      a[k + 4] = csub(e[k], o[k]);
+    }
+  }
+};
+
+// multiply by exp(-+ 2 pi i e / 16)
+template <int E, bool INV>
+__device__ __forceinline__ float2 w16(float2 v) {
+  const float c1 = 0.92387953251128675613f;  // cos(pi/8)
+  const float s1 = 0.38268343236508977173f;  // sin(pi/8)
+  if (E == 0) return v;
+  if (E % 2 == 0) return w8<E / 2, INV>(v);
+  // angle = 2 pi E / 16; (cr, si) = (cos, sin)
+  const float cr = (E == 1) ? c1 : (E == 3) ? s1 : (E == 9) ? -c1 : 0.f;
+  const float si = (E == 1) ? s1 : (E == 3) ? c1 : (E == 9) ? -s1 : 0.f;
+  // forward multiplies by (cr - i si), inverse by (cr + i si)
+  return INV ? make_float2(cr * v.x - si * v.y, cr * v.y + si * v.x)
+             : make_float2(cr * v.x + si * v.y, cr * v.y - si * v.x);
+}
+
+template <bool INV> struct Dft<16, INV> {
+  // 16 = 4 x 4: inner DFT4 over a[4 n1 + n2], twiddle W16^(n2 k1), outer DFT4 over n2
+  static __device__ __forceinline__ void run(float2* a) {
+    float2 y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      float2 t[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+      Dft<4, INV>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
+    }
+    y[1][1] = w16<1, INV>(y[1][1]);
+    y[1][2] = w16<2, INV>(y[1][2]);
+    y[1][3] = w16<3, INV>(y[1][3]);
+    y[2][1] = w16<2, INV>(y[2][1]);
+    y[2][2] = w16<4, INV>(y[2][2]);
+    y[2][3] = w16<6, INV>(y[2][3]);
+    y[3][1] = w16<3, INV>(y[3][1]);
+    y[3][2] = w16<6, INV>(y[3][2]);
+    y[3][3] = w16<9, INV>(y[3][3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Dft<4, INV>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
+    }
+  }
+};
+
+// ------------------------------------------------------------------ stages
+// Stage S of the Stockham transform; NS = product of the radices before it.
+// Butterfly j reads x[j + r N/R], multiplies by W_N^((j mod NS) r N/(NS R)),
+// applies the R-point DFT and writes x[(j/NS) NS R + (j mod NS) + r NS].
+// Thread t owns butterflies j = t + T b (b < V/R), whose inputs are its
+// canonical slots b + r V/R; the last stage's outputs land in canonical slots.
+template <int N, int V, int S, int NS, bool INV>
+struct Stage {
+  static __device__ __forceinline__ void run(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
+    constexpr int R = radix_at(N, V, S);
+    constexpr int T = N / V;
+    constexpr int B = V / R;
+    constexpr bool LAST = (S == num_stages(N, V) - 1);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      float2 a[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[r] = v[b + r * B];
+      const int j = t + T * b;
+      if (NS > 1) {
+        const int step = (j % NS) * (N / (NS * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(tw + step * r);
+          if (INV) w.y = -w.y;
+          a[r] = cmul(a[r], w);
+        }
+      }
+      Dft<R, INV>::run(a);
+      if (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b + r * B] = a[r];
+      } else {
+        const int p = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[pidx(p + r * NS)] = a[r];
+      }
+    }
+    if constexpr (!LAST) {
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < V; ++m) v[m] = sm[pidx(t + T * m)];
+      __syncthreads();
+      Stage<N, V, S + 1, NS * R, INV>::run(v, sm, t, tw);
+    }
+  }
+};
+
+// Unnormalised line DFT, sign -1 (forward) or +1 (INV).  Every thread of the
+// CTA must call it (it contains __syncthreads when the plan has >1 stage).
+// tw[e] = exp(-2 pi i e / N), e < N.  sm: this line's padded buffer.
+template <int N, int V, bool INV>
+__device__ __forceinline__ void fft_line(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
+  static_assert(N % V == 0, "V must divide N");
+  static_assert(num_stages(N, V) > 0, "no radix plan");
+  Stage<N, V, 0, 1, INV>::run(v, sm, t, tw);
+}
+
+}  // namespace fftenkf
