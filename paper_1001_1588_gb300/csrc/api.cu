@@ -140,7 +140,7 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
     }
   }
   const int nf = p->n_obs + 2 * p->n_obs * p->n_un;
-  if (p->n_obs > 0 && col_stats_smem(p->ny, nf, nullptr) == 0) {
+  if (p->n_obs > 0 && (col_stats_smem(p->ny, nf, nullptr) == 0 || col_update_smem(p->ny, p->n_obs, nullptr, nullptr) == 0)) {
     delete p;
     return fail(FFTENKF_EUNSUPPORTED, "covariance tables per column exceed shared memory (reduce blocks or ny)");
   }
@@ -245,7 +245,7 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   rp.n_obs = p->n_obs; rp.mode = kAnomaly; rp.storage = p->storage;
   rp.ens = ens; rp.mean = mp.mean;
   rp.out = reinterpret_cast<float2*>(ws + p->off_A);
-  rp.twL = p->twL(); rp.twX = p->twX();
+  rp.twL = p->twL(); rp.twX = p->twX(); rp.status = p->d_status;
   prof_begin(p, kPassRowAnom, s);
   e = launch_row_fwd(rp, p->M * p->N, s);
   prof_end(p, kPassRowAnom, s);
@@ -324,7 +324,7 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   for (int i = 0; i < p->n_obs; ++i) rp.obs[i] = p->obs[i];
   rp.ens = ensemble; rp.data = data; rp.pert = perturbations;
   rp.out = reinterpret_cast<float2*>(ws + p->off_W);
-  rp.twL = p->twL(); rp.twX = p->twX();
+  rp.twL = p->twL(); rp.twX = p->twX(); rp.status = p->d_status;
   prof_begin(p, kPassRowInnov, s);
   if (e == cudaSuccess) e = launch_row_fwd(rp, p->N * p->n_obs, s);
   prof_end(p, kPassRowInnov, s);
@@ -338,14 +338,14 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   }
   up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
-  up.twY = p->twY();
+  up.twY = p->twY(); up.status = p->d_status;
   prof_begin(p, kPassUpdate, s);
   if (e == cudaSuccess) e = launch_col_update(up, s);
   prof_end(p, kPassUpdate, s);
   RowInvParams ip;
   memset(&ip, 0, sizeof(ip));
   ip.ny = p->ny; ip.nx = p->nx; ip.L = p->L; ip.M = p->M; ip.N = p->N; ip.storage = p->storage;
-  ip.in = up.S; ip.ens = ensemble; ip.twL = p->twL(); ip.twX = p->twX();
+  ip.in = up.S; ip.ens = ensemble; ip.twL = p->twL(); ip.twX = p->twX(); ip.status = p->d_status;
   prof_begin(p, kPassRowInv, s);
   if (e == cudaSuccess) e = launch_row_inv(ip, p->M * p->N, s);
   prof_end(p, kPassRowInv, s);
@@ -362,6 +362,7 @@ extern "C" fftenkf_status fftenkf_last_device_status(fftenkf_plan p, void* strea
   e = cudaMemcpy(&word, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "status word");
+  if (word & kStatusTimeout) return fail(FFTENKF_ETIMEOUT, "a bounded wait for an asynchronous copy gave up");
   if (word & kStatusNonFinite) return fail(FFTENKF_ENONFINITE, "non-finite spectral covariance");
   return FFTENKF_OK;
 }

@@ -25,7 +25,7 @@ enum RowMode { kAnomaly = 0, kInnovation = 1 };
 enum Storage { kF32 = 0, kBF16 = 1 };
 
 // Status bits written by kernels (OR-ed into the plan's device word).
-enum DeviceStatusBits { kStatusNonFinite = 1 };
+enum DeviceStatusBits { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
 __device__ __forceinline__ float2 load2(const void* base, size_t idx, int storage) {
   // two consecutive elements idx, idx+1 (idx even)
@@ -65,6 +65,7 @@ struct RowFwdParams {
   float2* out;            // row spectra: anomaly field j*N+k, innovation field k*n_obs+i
   const float2* twL;      // exp(-2 pi i e / L), e < L
   const float2* twX;      // exp(-2 pi i k / nx), k <= L
+  int* status;
 };
 
 struct RowInvParams {
@@ -73,6 +74,7 @@ struct RowInvParams {
   void* ens;              // [M][N][ny][nx], updated in place
   const float2* twL;
   const float2* twX;
+  int* status;
 };
 
 struct ColStatsParams {
@@ -95,6 +97,8 @@ struct ColUpdParams {
   const float2* gjo;      // [n_obs*n_un][L+1][ny], table i*n_un+u
   float2* S;              // increment row spectra, field j*N+k
   const float2* twY;
+  int* status;
+  int n_stages;           // innovation prefetch stages (set by the launcher)
 };
 
 struct GainParams {
@@ -121,5 +125,6 @@ bool line_supported(int n);       // column line lengths
 bool row_line_supported(int n);   // row line lengths (nx/2)
 // shared-memory bytes a pass needs (0 = unsupported), for plan-time checks
 size_t col_stats_smem(int ny, int nf, int* lpc);
+size_t col_update_smem(int ny, int n_obs, int* lpc, int* n_stages);
 
 }  // namespace fftenkf

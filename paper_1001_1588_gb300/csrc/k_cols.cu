@@ -4,18 +4,49 @@
 
 namespace fftenkf {
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+static size_t padded_bytes(int ny) { return (size_t)((padded_len(ny) + 1) & ~1) * sizeof(float2); }
+
+// per group: accumulators nf*ny floats, exchange line, one prefetch line
 size_t col_stats_smem(int ny, int nf, int* lpc) {
   const int V = default_V(ny);
   const int T = ny / V;
-  const size_t per = ((size_t)nf * ny + 2 * (size_t)padded_len(ny)) * sizeof(float);
-  int want = 256 / T;
-  if (want < 1) want = 1;
-  const size_t cap = 200 * 1024;
-  int n = want;
-  while (n > 1 && n * per > cap) n >>= 1;
-  if (n * per > 227 * 1024) return 0;
+  const size_t per = (size_t)nf * ny * sizeof(float) + padded_bytes(ny) + (size_t)ny * sizeof(float2);
+  int n = 256 / T;
+  if (n < 1) n = 1;
+  while (n > 1 && n * per + 16 > 200 * 1024) n >>= 1;
+  if (n * per + 16 > 227 * 1024) return 0;
   if (lpc) *lpc = n;
-  return n * per;
+  return n * per + 16;
+}
+
+// per group: one or two stages of n_obs innovation lines, one stage of gain lines, exchange line
+size_t col_update_smem(int ny, int n_obs, int* lpc, int* n_stages) {
+  const int V = default_V(ny);
+  const int T = ny / V;
+  const size_t lines = (size_t)n_obs * ny * sizeof(float2);
+  for (int nst = 2; nst >= 1; --nst) {
+    const size_t per = (nst + 1) * lines + padded_bytes(ny);
+    int n = 256 / T;
+    if (n < 1) n = 1;
+    while (n > 1 && n * per + 32 > 200 * 1024) n >>= 1;
+    if (n * per + 32 <= 227 * 1024) {
+      if (lpc) *lpc = n;
+      if (n_stages) *n_stages = nst;
+      return n * per + 32;
+    }
+  }
+  return 0;
 }
 
 cudaError_t launch_col_stats(const ColStatsParams& p, cudaStream_t s) {

@@ -1,5 +1,8 @@
 // Column passes: the second half of each 2-D transform, fused with the
-// per-wavenumber work of Sec. 2.1.
+// per-wavenumber work of Sec. 2.1.  Both are persistent kernels whose input
+// lines (one wavenumber column k_x of a field's row spectra, ny contiguous
+// complex values) arrive in shared memory by bulk asynchronous copies issued
+// one step ahead, so HBM latency overlaps the transforms.
 //
 // col_stats (steps 1-2, eq. dii and eq. cov-multi-spectral): a thread group
 // owns one wavenumber column k_x and loops over the members; for each member
@@ -15,173 +18,312 @@
 // transform for every target block and writes the increment's row spectra.
 #pragma once
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace fftenkf {
 
 template <int NY, int V>
-__device__ __forceinline__ void load_col(float2 (&v)[V], const float2* __restrict__ src, int t, int part,
-                                         bool active) {
+__device__ __forceinline__ void read_line(float2 (&v)[V], const float2* __restrict__ src, int t, int part) {
   constexpr int T = NY / V;
 #pragma unroll
   for (int m = 0; m < V; ++m) {
-    float2 a = active ? src[t + T * m] : make_float2(0.f, 0.f);
+    float2 a = src[t + T * m];
     if (part == 1) a = make_float2(a.x, 0.f);
     if (part == 2) a = make_float2(a.y, 0.f);
     v[m] = a;
   }
 }
 
+// ----------------------------------------------------------------- col_stats
+// smem: acc [LPC][nf][NY] f32 | xbuf [LPC][padded(NY)] f2 | stage [LPC][NY] f2 | bar | flag
 template <int NY, int V, int NOBS>
-__global__ void __launch_bounds__(256) col_stats_kernel(const ColStatsParams p) {
+__global__ void __launch_bounds__(256, 1) col_stats_kernel(const ColStatsParams p) {
   constexpr int T = NY / V;
-  extern __shared__ float smf[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
-  const int c = blockIdx.x * LPC + g;            // wavenumber column k_x in [0, L]
-  const bool active = c <= p.L;
   const int nf = p.n_obs + 2 * p.n_obs * p.n_un;
-  float* acc = smf + (size_t)g * ((size_t)nf * NY + 2 * padded_len(NY));
+  float* acc_all = reinterpret_cast<float*>(smraw);
+  float* acc = acc_all + (size_t)g * nf * NY;
   float2* xacc = reinterpret_cast<float2*>(acc + p.n_obs * NY);
-  float2* line = reinterpret_cast<float2*>(acc + (size_t)nf * NY);
-  for (int s = t; s < nf * NY; s += T) acc[s] = 0.f;
-  const int col = (c == p.L) ? 0 : c;
-  const int part = (c == 0) ? 1 : ((c == p.L) ? 2 : 0);
+  float2* xbuf_all = reinterpret_cast<float2*>(acc_all + (size_t)LPC * nf * NY);
+  constexpr int PL = (padded_len(NY) + 1) & ~1;
+  float2* line = xbuf_all + (size_t)g * PL;
+  float2* stage_all = xbuf_all + (size_t)LPC * PL;
+  float2* stage = stage_all + (size_t)g * NY;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage_all + (size_t)LPC * NY);
+  int* flag = reinterpret_cast<int*>(bar + 1);
+  const int M = p.M;
+  const int lines_per_col = p.N * M;
   const size_t fstride = (size_t)p.L * NY;
-  for (int k = 0; k < p.N; ++k) {
+  const int ncol = p.L + 1;
+  const int col_step = gridDim.x * LPC;
+
+  // global line l of column group starting at cb: member k = l / M, block slot b = l % M
+  auto issue = [&](int cb, int l) {
+    const int k = l / M, b = l - (l / M) * M;
+    const int blk = (b < p.n_obs) ? p.obs[b] : p.un[b - p.n_obs];
+    int nvalid = 0;
+    for (int gg = 0; gg < LPC; ++gg) nvalid += (cb + gg < ncol);
+    mbar_arrive_expect_tx(bar, (uint32_t)(nvalid * NY * sizeof(float2)));
+    for (int gg = 0; gg < LPC; ++gg) {
+      const int c = cb + gg;
+      if (c >= ncol) break;
+      const int col = (c == p.L) ? 0 : c;
+      bulk_g2s(stage_all + (size_t)gg * NY, p.A + ((size_t)blk * p.N + k) * fstride + (size_t)col * NY,
+               NY * sizeof(float2), bar);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int cb = blockIdx.x * LPC;
+  if (threadIdx.x == 0 && cb < ncol) issue(cb, 0);
+  for (; cb < ncol; cb += col_step) {
+    const int c = cb + g;
+    const bool active = c < ncol;
+    const int part = (c == 0) ? 1 : ((c == p.L) ? 2 : 0);
+    for (int s = t; s < nf * NY; s += T) acc[s] = 0.f;
     float2 ko[NOBS][V];
 #pragma unroll
-    for (int i = 0; i < NOBS; ++i) {
-      if (i < p.n_obs) {
-        float2 v[V];
-        load_col<NY, V>(v, p.A + ((size_t)p.obs[i] * p.N + k) * fstride + (size_t)col * NY, t, part, active);
-        fft_line<NY, V, false>(v, line, t, p.twY);
+    for (int i = 0; i < NOBS; ++i)
 #pragma unroll
-        for (int m = 0; m < V; ++m) {
-          ko[i][m] = v[m];
-          acc[i * NY + t + T * m] += v[m].x * v[m].x + v[m].y * v[m].y;
-        }
-      }
-    }
-    for (int u = 0; u < p.n_un; ++u) {
+      for (int m = 0; m < V; ++m) ko[i][m] = make_float2(0.f, 0.f);
+    for (int l = 0; l < lines_per_col; ++l) {
+      const int b = l % M;
+      if (!cta_wait(bar, phase, p.status, flag)) return;
+      phase ^= 1;
       float2 v[V];
-      load_col<NY, V>(v, p.A + ((size_t)p.un[u] * p.N + k) * fstride + (size_t)col * NY, t, part, active);
+      read_line<NY, V>(v, stage, t, part);
+      __syncthreads();                                   // stage consumed
+      if (threadIdx.x == 0) {
+        if (l + 1 < lines_per_col) issue(cb, l + 1);
+        else if (cb + col_step < ncol) issue(cb + col_step, 0);
+      }
       fft_line<NY, V, false>(v, line, t, p.twY);
+      if (b < p.n_obs) {
 #pragma unroll
-      for (int i = 0; i < NOBS; ++i) {
-        if (i < p.n_obs) {
-          float2* a = xacc + (size_t)(i * p.n_un + u) * NY + t;
+        for (int i = 0; i < NOBS; ++i) {
+          if (i == b) {
 #pragma unroll
-          for (int m = 0; m < V; ++m) {
-            const float2 cr = cmulc(v[m], ko[i][m]);
-            a[T * m].x += cr.x;
-            a[T * m].y += cr.y;
+            for (int m = 0; m < V; ++m) {
+              ko[i][m] = v[m];
+              acc[i * NY + t + T * m] += v[m].x * v[m].x + v[m].y * v[m].y;
+            }
+          }
+        }
+      } else {
+        const int u = b - p.n_obs;
+#pragma unroll
+        for (int i = 0; i < NOBS; ++i) {
+          if (i < p.n_obs) {
+            float2* a = xacc + (size_t)(i * p.n_un + u) * NY + t;
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+              const float2 cr = cmulc(v[m], ko[i][m]);
+              float2 o = a[T * m];
+              o.x += cr.x;
+              o.y += cr.y;
+              a[T * m] = o;
+            }
           }
         }
       }
     }
-  }
-  if (!active) return;
-  const size_t tab = (size_t)(p.L + 1) * NY;
-  bool bad = false;
-  for (int i = 0; i < p.n_obs; ++i) {
+    if (active) {
+      const size_t tab = (size_t)(p.L + 1) * NY;
+      bool bad = false;
+      for (int i = 0; i < p.n_obs; ++i) {
 #pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const int ky = t + T * m;
-      const float val = acc[i * NY + ky] * p.scale;
-      bad |= !isfinite(val);
-      p.chat[i * tab + (size_t)c * NY + ky] = val;
-    }
-  }
-  float2* xout = reinterpret_cast<float2*>(p.chat + p.n_obs * tab);
-  for (int q = 0; q < p.n_obs * p.n_un; ++q) {
+        for (int m = 0; m < V; ++m) {
+          const int ky = t + T * m;
+          const float val = acc[i * NY + ky] * p.scale;
+          bad |= !isfinite(val);
+          p.chat[i * tab + (size_t)c * NY + ky] = val;
+        }
+      }
+      float2* xout = reinterpret_cast<float2*>(p.chat + p.n_obs * tab);
+      for (int q = 0; q < p.n_obs * p.n_un; ++q) {
 #pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const int ky = t + T * m;
-      const float2 a = xacc[(size_t)q * NY + ky];
-      const float2 val = make_float2(a.x * p.scale, a.y * p.scale);
-      bad |= !(isfinite(val.x) && isfinite(val.y));
-      xout[q * tab + (size_t)c * NY + ky] = val;
+        for (int m = 0; m < V; ++m) {
+          const int ky = t + T * m;
+          const float2 a = xacc[(size_t)q * NY + ky];
+          const float2 val = make_float2(a.x * p.scale, a.y * p.scale);
+          bad |= !(isfinite(val.x) && isfinite(val.y));
+          xout[q * tab + (size_t)c * NY + ky] = val;
+        }
+      }
+      if (bad) atomicOr(p.status, kStatusNonFinite);
     }
+    __syncthreads();
   }
-  if (bad) atomicOr(p.status, kStatusNonFinite);
 }
 
+// ----------------------------------------------------------------- col_update
+// Two bulk-copy pipelines: innovation lines one item ahead (two stages, or one
+// when shared memory is short) and gain lines one target block ahead (one
+// stage, read into registers before the next copy is issued).
+// smem: wst [nst][LPC][n_obs][NY] f2 | gst [LPC][n_obs][NY] f2 | xbuf [LPC][PL] f2 | bars[3] | flag
 template <int NY, int V, int NOBS>
-__global__ void __launch_bounds__(256) col_update_kernel(const ColUpdParams p) {
+__global__ void __launch_bounds__(256, 1) col_update_kernel(const ColUpdParams p) {
   constexpr int T = NY / V;
-  extern __shared__ float2 sm2[];
+  constexpr int PL = (padded_len(NY) + 1) & ~1;
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
-  const int item = blockIdx.x * LPC + g;
-  const int c = item / p.N;
-  const int k = item - c * p.N;
-  const bool active = c <= p.L;
-  float2* line = sm2 + (size_t)g * padded_len(NY);
-  const int col = (c == p.L) ? 0 : c;
-  const int part = (c == 0) ? 1 : ((c == p.L) ? 2 : 0);
+  const int nst = p.n_stages;
+  const size_t stage_elems = (size_t)LPC * p.n_obs * NY;
+  float2* wst = reinterpret_cast<float2*>(smraw);
+  float2* gst = wst + nst * stage_elems;
+  float2* xbuf = gst + stage_elems + (size_t)g * PL;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gst + stage_elems + (size_t)LPC * PL);
+  uint64_t* gbar = bars + 2;
+  int* flag = reinterpret_cast<int*>(bars + 3);
+  const long long n_items = (long long)(p.L + 1) * p.N;
+  const long long step = (long long)gridDim.x * LPC;
   const size_t fstride = (size_t)p.L * NY;
   const size_t tab = (size_t)(p.L + 1) * NY;
-  const size_t cc = active ? (size_t)c * NY : 0;
-  float2 w[NOBS][V];
-#pragma unroll
-  for (int i = 0; i < NOBS; ++i) {
-    if (i < p.n_obs) {
-      float2 v[V];
-      load_col<NY, V>(v, p.W + ((size_t)k * p.n_obs + i) * fstride + (size_t)col * NY, t, part, active);
-      fft_line<NY, V, false>(v, line, t, p.twY);
-#pragma unroll
-      for (int m = 0; m < V; ++m) w[i][m] = v[m];
+
+  auto issue_w = [&](long long base, int s) {
+    int nvalid = 0;
+    for (int gg = 0; gg < LPC; ++gg) nvalid += (base + gg < n_items);
+    mbar_arrive_expect_tx(&bars[s], (uint32_t)(nvalid * p.n_obs * NY * sizeof(float2)));
+    for (int gg = 0; gg < LPC; ++gg) {
+      const long long item = base + gg;
+      if (item >= n_items) break;
+      const int c = (int)(item / p.N), k = (int)(item - (long long)c * p.N);
+      const int col = (c == p.L) ? 0 : c;
+      for (int i = 0; i < p.n_obs; ++i)
+        bulk_g2s(wst + s * stage_elems + ((size_t)gg * p.n_obs + i) * NY,
+                 p.W + ((size_t)k * p.n_obs + i) * fstride + (size_t)col * NY, NY * sizeof(float2), &bars[s]);
     }
-  }
-  for (int j = 0; j < p.M; ++j) {
-    float2 s[V];
+  };
+  // gain lines of target block j for every group's item: observed j -> one float line,
+  // unobserved j -> n_obs complex lines
+  auto issue_g = [&](long long base, int j) {
     const int io = p.obs_of_block[j];
-#pragma unroll
-    for (int m = 0; m < V; ++m) s[m] = make_float2(0.f, 0.f);
-    if (io >= 0) {
-      const float* gp = p.goo + io * tab + cc + t;
-#pragma unroll
-      for (int i = 0; i < NOBS; ++i) {
-        if (i == io) {
-#pragma unroll
-          for (int m = 0; m < V; ++m) {
-            const float gv = active ? __ldg(gp + T * m) : 0.f;
-            s[m] = make_float2(gv * w[i][m].x, gv * w[i][m].y);
-          }
-        }
-      }
-    } else {
-      const int u = p.un_of_block[j];
-#pragma unroll
-      for (int i = 0; i < NOBS; ++i) {
-        if (i < p.n_obs) {
-          const float2* gp = p.gjo + (size_t)(i * p.n_un + u) * tab + cc + t;
-#pragma unroll
-          for (int m = 0; m < V; ++m) {
-            const float2 gv = active ? __ldg(gp + T * m) : make_float2(0.f, 0.f);
-            s[m] = cadd(s[m], cmul(gv, w[i][m]));
-          }
-        }
-      }
-    }
-    fft_line<NY, V, true>(s, line, t, p.twY);
-    if (active) {
-      float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * NY + t;
-      if (part == 0) {
-#pragma unroll
-        for (int m = 0; m < V; ++m) dst[T * m] = s[m];
+    const uint32_t line_bytes = (io >= 0) ? NY * sizeof(float) : NY * sizeof(float2);
+    const int nl = (io >= 0) ? 1 : p.n_obs;
+    int nvalid = 0;
+    for (int gg = 0; gg < LPC; ++gg) nvalid += (base + gg < n_items);
+    mbar_arrive_expect_tx(gbar, (uint32_t)(nvalid * nl) * line_bytes);
+    for (int gg = 0; gg < LPC; ++gg) {
+      const long long item = base + gg;
+      if (item >= n_items) break;
+      const int c = (int)(item / p.N);
+      float2* dst = gst + (size_t)gg * p.n_obs * NY;
+      if (io >= 0) {
+        bulk_g2s(dst, p.goo + io * tab + (size_t)c * NY, line_bytes, gbar);
       } else {
-        float* d1 = reinterpret_cast<float*>(dst) + (part == 1 ? 0 : 1);
-#pragma unroll
-        for (int m = 0; m < V; ++m) d1[2 * T * m] = s[m].x;
+        const int u = p.un_of_block[j];
+        for (int i = 0; i < p.n_obs; ++i)
+          bulk_g2s(dst + (size_t)i * NY, p.gjo + (size_t)(i * p.n_un + u) * tab + (size_t)c * NY, line_bytes, gbar);
       }
     }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(gbar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t wph0 = 0, wph1 = 0, gph = 0;
+  long long base = (long long)blockIdx.x * LPC;
+  if (threadIdx.x == 0 && base < n_items) {
+    issue_w(base, 0);
+    issue_g(base, 0);
+  }
+  for (int it = 0; base < n_items; base += step, ++it) {
+    const int s = (nst == 2) ? (it & 1) : 0;
+    if (!cta_wait(&bars[s], s ? wph1 : wph0, p.status, flag)) {
+      if (threadIdx.x == 0) {   // other copies may still be landing: let them finish
+        mbar_wait_bounded(&bars[s ^ 1], s ? wph0 : wph1);
+        mbar_wait_bounded(gbar, gph);
+      }
+      return;
+    }
+    if (s) wph1 ^= 1; else wph0 ^= 1;
+    if (nst == 2 && threadIdx.x == 0 && base + step < n_items) issue_w(base + step, s ^ 1);
+    const long long item = base + g;
+    const bool active = item < n_items;
+    const int c = active ? (int)(item / p.N) : 0;
+    const int k = active ? (int)(item - (long long)c * p.N) : 0;
+    const int col = (c == p.L) ? 0 : c;
+    const int part = (c == 0) ? 1 : ((c == p.L) ? 2 : 0);
+    float2* w = wst + s * stage_elems + (size_t)g * p.n_obs * NY;
+    const float2* gl = gst + (size_t)g * p.n_obs * NY;
+    // forward column transforms of the innovations, kept in place in the stage
+    for (int i = 0; i < p.n_obs; ++i) {
+      float2 v[V];
+      read_line<NY, V>(v, w + (size_t)i * NY, t, part);
+      fft_line<NY, V, false>(v, xbuf, t, p.twY);
+#pragma unroll
+      for (int m = 0; m < V; ++m) w[(size_t)i * NY + t + T * m] = v[m];
+    }
+    for (int j = 0; j < p.M; ++j) {
+      if (!cta_wait(gbar, gph, p.status, flag)) {
+        if (threadIdx.x == 0) {
+          mbar_wait_bounded(&bars[0], wph0);
+          mbar_wait_bounded(&bars[1], wph1);
+        }
+        return;
+      }
+      gph ^= 1;
+      float2 sv[V];
+      const int io = p.obs_of_block[j];
+      if (io >= 0) {
+        const float* gp = reinterpret_cast<const float*>(gl) + t;
+        const float2* wp = w + (size_t)io * NY + t;
+#pragma unroll
+        for (int m = 0; m < V; ++m) {
+          const float gv = gp[T * m];
+          const float2 x = wp[T * m];
+          sv[m] = make_float2(gv * x.x, gv * x.y);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < V; ++m) sv[m] = make_float2(0.f, 0.f);
+        for (int i = 0; i < p.n_obs; ++i) {
+          const float2* gp = gl + (size_t)i * NY + t;
+          const float2* wp = w + (size_t)i * NY + t;
+#pragma unroll
+          for (int m = 0; m < V; ++m) sv[m] = cadd(sv[m], cmul(gp[T * m], wp[T * m]));
+        }
+      }
+      __syncthreads();   // gain stage consumed
+      if (threadIdx.x == 0) {
+        if (j + 1 < p.M) issue_g(base, j + 1);
+        else if (base + step < n_items) issue_g(base + step, 0);
+      }
+      fft_line<NY, V, true>(sv, xbuf, t, p.twY);
+      if (active) {
+        float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * NY + t;
+        if (part == 0) {
+#pragma unroll
+          for (int m = 0; m < V; ++m) dst[T * m] = sv[m];
+        } else {
+          float* d1 = reinterpret_cast<float*>(dst) + (part == 1 ? 0 : 1);
+#pragma unroll
+          for (int m = 0; m < V; ++m) d1[2 * T * m] = sv[m].x;
+        }
+      }
+    }
+    __syncthreads();
+    if (nst == 1 && threadIdx.x == 0 && base + step < n_items) issue_w(base + step, 0);
   }
 }
 
 // ----------------------------------------------------------------- launch templates
+int sm_count();
+
 template <int NY, int NOBS>
 inline cudaError_t col_stats_NY(const ColStatsParams& p, cudaStream_t st) {
   constexpr int V = default_V(NY);
@@ -193,24 +335,38 @@ inline cudaError_t col_stats_NY(const ColStatsParams& p, cudaStream_t st) {
   auto kern = col_stats_kernel<NY, V, NOBS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = (p.L + 1 + lpc - 1) / lpc;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T * lpc, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int groups = (p.L + 1 + lpc - 1) / lpc;
+  int grid = sm_count() * per_sm;
+  if (grid > groups) grid = groups;
   kern<<<grid, T * lpc, smem, st>>>(p);
   return cudaGetLastError();
 }
+
+size_t col_update_smem(int ny, int n_obs, int* lpc, int* n_stages);
 
 template <int NY, int NOBS>
 inline cudaError_t col_update_NY(const ColUpdParams& p, cudaStream_t st) {
   constexpr int V = default_V(NY);
   constexpr int T = NY / V;
-  int lpc = 256 / T;
-  if (lpc < 1) lpc = 1;
-  const size_t smem = (size_t)lpc * padded_len(NY) * sizeof(float2);
+  int lpc = 1, nst = 2;
+  const size_t smem = col_update_smem(NY, p.n_obs, &lpc, &nst);
+  if (smem == 0) return cudaErrorInvalidConfiguration;
+  ColUpdParams q = p;
+  q.n_stages = nst;
   auto kern = col_update_kernel<NY, V, NOBS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T * lpc, smem);
+  if (per_sm < 1) per_sm = 1;
   const long long items = (long long)(p.L + 1) * p.N;
-  const long long grid = (items + lpc - 1) / lpc;
-  kern<<<(unsigned)grid, T * lpc, smem, st>>>(p);
+  const long long groups = (items + lpc - 1) / lpc;
+  long long grid = (long long)sm_count() * per_sm;
+  if (grid > groups) grid = groups;
+  kern<<<(unsigned)grid, T * lpc, smem, st>>>(q);
   return cudaGetLastError();
 }
 
@@ -236,7 +392,6 @@ inline cudaError_t col_update_dispatch(const ColUpdParams& p, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
 }
-
 
 cudaError_t col_stats_nobs1(const ColStatsParams& p, cudaStream_t s);
 cudaError_t col_stats_nobs2(const ColStatsParams& p, cudaStream_t s);

@@ -11,6 +11,7 @@
 // The inverse row pass does the same in reverse and adds the increment to the
 // forecast member in the same pass.
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace fftenkf {
 
@@ -74,174 +75,277 @@ cudaError_t launch_mean(const MeanParams& p, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------- rows
+// Persistent CTAs walk the tiles (member fastest, so the CTAs working on the
+// same rows of different members run together and share the mean or data rows
+// through L2).  Each tile of R rows is done in rounds of LPC rows; the
+// per-member input rows of the next round (u, and e for innovations) are bulk
+// copied into a shared-memory stage while the current round is transformed.
+struct RowTile {
+  int k, tile, jb;
+};
+
+__device__ __forceinline__ RowTile decode_tile(long long q, int N, int n_tiles) {
+  RowTile r;
+  r.k = (int)(q % N);
+  q /= N;
+  r.tile = (int)(q % n_tiles);
+  r.jb = (int)(q / n_tiles);
+  return r;
+}
+
 template <int L, int V>
-__global__ void __launch_bounds__(512) row_fwd_kernel(const RowFwdParams p) {
+__global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   constexpr int T = L / V;
-  extern __shared__ float2 sm[];
-  const int pitch = padded_len(L) + 1;
+  constexpr int pitch = padded_len(L) + 1;
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
+  const int rounds = p.R / LPC;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
-  int b = blockIdx.x;
-  const int k = b % p.N;
-  b /= p.N;
-  const int tile = b % p.n_tiles;
-  const int jb = b / p.n_tiles;       // block j (anomaly) or observed index i (innovation)
-  const int y0 = tile * p.R;
-  const size_t G = (size_t)p.ny * p.nx;
-  size_t f;
-  const void* u;
-  const float* mu = nullptr;
-  const float* d = nullptr;
-  const void* e = nullptr;
-  if (p.mode == kAnomaly) {
-    f = (size_t)jb * p.N + k;
-    u = (p.storage == kBF16) ? (const void*)((const __nv_bfloat16*)p.ens + f * G)
-                             : (const void*)((const float*)p.ens + f * G);
-    mu = p.mean + (size_t)jb * G;
-  } else {
-    f = (size_t)k * p.n_obs + jb;
-    const size_t fu = (size_t)p.obs[jb] * p.N + k;
-    u = (p.storage == kBF16) ? (const void*)((const __nv_bfloat16*)p.ens + fu * G)
-                             : (const void*)((const float*)p.ens + fu * G);
-    d = p.data + (size_t)jb * G;
-    e = (p.storage == kBF16) ? (const void*)((const __nv_bfloat16*)p.pert + f * G)
-                             : (const void*)((const float*)p.pert + f * G);
-  }
-  for (int r0 = 0; r0 < p.R; r0 += LPC) {
-    const int r = r0 + g;
-    const size_t rowoff = (size_t)(y0 + r) * p.nx;
-    float2 v[V];
-#pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const size_t idx = rowoff + 2 * (size_t)(t + T * m);
-      const float2 a = load2(u, idx, p.storage);
-      if (p.mode == kAnomaly) {
-        const float2 c = *reinterpret_cast<const float2*>(mu + idx);
-        v[m] = make_float2(a.x - c.x, a.y - c.y);
-      } else {
-        const float2 dd = *reinterpret_cast<const float2*>(d + idx);
-        const float2 ee = load2(e, idx, p.storage);
-        v[m] = make_float2((dd.x + ee.x) - a.x, (dd.y + ee.y) - a.y);
-      }
+  const int nx = p.nx;
+  const size_t G = (size_t)p.ny * nx;
+  const int es = (p.storage == kBF16) ? 2 : 4;
+  const int n_in = (p.mode == kAnomaly) ? 1 : 2;
+  const uint32_t round_bytes = (uint32_t)LPC * nx * es;
+  float2* lines = reinterpret_cast<float2*>(smraw);
+  unsigned char* stage = smraw + (((size_t)p.R * pitch * sizeof(float2) + 127) & ~(size_t)127);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)n_in * round_bytes);
+  int* flag = reinterpret_cast<int*>(bar + 1);
+  const int n_jb = (p.mode == kAnomaly) ? p.M : p.n_obs;
+  const long long Q = (long long)n_jb * p.n_tiles * p.N;
+  const char* ens = reinterpret_cast<const char*>(p.ens);
+  const char* pert = reinterpret_cast<const char*>(p.pert);
+
+  auto issue = [&](long long q, int r) {
+    const RowTile w = decode_tile(q, p.N, p.n_tiles);
+    const size_t row0 = (size_t)w.tile * p.R + (size_t)r * LPC;
+    const size_t fu = (p.mode == kAnomaly) ? (size_t)w.jb * p.N + w.k : (size_t)p.obs[w.jb] * p.N + w.k;
+    mbar_arrive_expect_tx(bar, n_in * round_bytes);
+    bulk_g2s(stage, ens + (fu * G + row0 * nx) * es, round_bytes, bar);
+    if (p.mode == kInnovation) {
+      const size_t fe = (size_t)w.k * p.n_obs + w.jb;
+      bulk_g2s(stage + round_bytes, pert + (fe * G + row0 * nx) * es, round_bytes, bar);
     }
-    float2* line = sm + r * pitch;
-    fft_line<L, V, false>(v, line, t, p.twL);
-#pragma unroll
-    for (int m = 0; m < V; ++m) line[pidx(t + T * m)] = v[m];
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
   }
   __syncthreads();
-  // spectrum of the real rows, written transposed: out[c][y0 + r]
-  float2* out = p.out + f * (size_t)L * p.ny + y0;
+  uint32_t phase = 0;
+  long long q = blockIdx.x;
+  if (threadIdx.x == 0 && q < Q) issue(q, 0);
   const int RP = p.R >> 1;
-  for (int idx = threadIdx.x; idx < L * RP; idx += blockDim.x) {
-    const int rp = idx % RP;
-    const int c = idx / RP;
-    const float2 w = __ldg(p.twX + c);
-    float2 res[2];
+  const int rp = threadIdx.x % RP;
+  const int cstep = blockDim.x / RP;
+  for (; q < Q; q += gridDim.x) {
+    const RowTile w = decode_tile(q, p.N, p.n_tiles);
+    const int y0 = w.tile * p.R;
+    const size_t f = (p.mode == kAnomaly) ? (size_t)w.jb * p.N + w.k : (size_t)w.k * p.n_obs + w.jb;
+    const float* shared_in = (p.mode == kAnomaly) ? p.mean + (size_t)w.jb * G : p.data + (size_t)w.jb * G;
+    for (int r = 0; r < rounds; ++r) {
+      const int row = r * LPC + g;
+      const float* sh = shared_in + (size_t)(y0 + row) * nx;
+      float2 sv[V];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float2* row = sm + (2 * rp + q) * pitch;
-      const float2 Z = row[pidx(c)];
-      if (c == 0) {
-        res[q] = make_float2(Z.x + Z.y, Z.x - Z.y);   // packed: X[0] + i X[L]
-      } else {
-        const float2 Zc = row[pidx(L - c)];
-        const float2 E = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y));
-        const float2 O = make_float2(0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x));
-        res[q] = cadd(E, cmul(w, O));
+      for (int m = 0; m < V; ++m) sv[m] = __ldg(reinterpret_cast<const float2*>(sh) + t + T * m);
+      if (!cta_wait(bar, phase, p.status, flag)) return;
+      phase ^= 1;
+      float2 v[V];
+      const unsigned char* st_row = stage + (size_t)g * nx * es;
+#pragma unroll
+      for (int m = 0; m < V; ++m) {
+        const size_t idx = 2 * (size_t)(t + T * m);
+        const float2 a = load2(st_row, idx, p.storage);
+        if (p.mode == kAnomaly) {
+          v[m] = make_float2(a.x - sv[m].x, a.y - sv[m].y);
+        } else {
+          const float2 ee = load2(st_row + round_bytes, idx, p.storage);
+          v[m] = make_float2((sv[m].x + ee.x) - a.x, (sv[m].y + ee.y) - a.y);
+        }
       }
+      __syncthreads();   // stage consumed
+      if (threadIdx.x == 0) {
+        if (r + 1 < rounds) issue(q, r + 1);
+        else if (q + gridDim.x < Q) issue(q + gridDim.x, 0);
+      }
+      float2* line = lines + row * pitch;
+      fft_line<L, V, false>(v, line, t, p.twL);
+#pragma unroll
+      for (int m = 0; m < V; ++m) line[pidx(t + T * m)] = v[m];
     }
-    *reinterpret_cast<float4*>(out + (size_t)c * p.ny + 2 * rp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+    __syncthreads();
+    // spectrum of the real rows, written transposed: out[c][y0 + r]
+    float2* out = p.out + f * (size_t)L * p.ny + y0 + 2 * rp;
+    const float2* r0 = lines + (2 * rp) * pitch;
+    const float2* r1 = r0 + pitch;
+    for (int c = threadIdx.x / RP; c < L; c += cstep) {
+      float2 res[2];
+      const float2 Z0 = r0[pidx(c)], Z1 = r1[pidx(c)];
+      if (c == 0) {
+        res[0] = make_float2(Z0.x + Z0.y, Z0.x - Z0.y);   // packed: X[0] + i X[L]
+        res[1] = make_float2(Z1.x + Z1.y, Z1.x - Z1.y);
+      } else {
+        const float2 wt = __ldg(p.twX + c);
+        const float2 C0 = r0[pidx(L - c)], C1 = r1[pidx(L - c)];
+        const float2 E0 = make_float2(0.5f * (Z0.x + C0.x), 0.5f * (Z0.y - C0.y));
+        const float2 O0 = make_float2(0.5f * (Z0.y + C0.y), -0.5f * (Z0.x - C0.x));
+        const float2 E1 = make_float2(0.5f * (Z1.x + C1.x), 0.5f * (Z1.y - C1.y));
+        const float2 O1 = make_float2(0.5f * (Z1.y + C1.y), -0.5f * (Z1.x - C1.x));
+        res[0] = cadd(E0, cmul(wt, O0));
+        res[1] = cadd(E1, cmul(wt, O1));
+      }
+      *reinterpret_cast<float4*>(out + (size_t)c * p.ny) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+    }
+    __syncthreads();
   }
 }
 
 template <int L, int V>
-__global__ void __launch_bounds__(512) row_inv_kernel(const RowInvParams p) {
+__global__ void __launch_bounds__(512, 1) row_inv_kernel(const RowInvParams p) {
   constexpr int T = L / V;
-  extern __shared__ float2 sm[];
-  const int pitch = padded_len(L) + 1;
+  constexpr int pitch = padded_len(L) + 1;
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
+  const int rounds = p.R / LPC;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
-  const int tile = blockIdx.x % p.n_tiles;
-  const size_t f = blockIdx.x / p.n_tiles;         // field j*N + k
-  const int y0 = tile * p.R;
-  const size_t G = (size_t)p.ny * p.nx;
-  const float2* in = p.in + f * (size_t)L * p.ny + y0;
-  const int RP = p.R >> 1;
-  for (int idx = threadIdx.x; idx < L * RP; idx += blockDim.x) {
-    const int rp = idx % RP;
-    const int c = idx / RP;
-    const float4 v4 = *reinterpret_cast<const float4*>(in + (size_t)c * p.ny + 2 * rp);
-    sm[(2 * rp) * pitch + pidx(c)] = make_float2(v4.x, v4.y);
-    sm[(2 * rp + 1) * pitch + pidx(c)] = make_float2(v4.z, v4.w);
+  const int nx = p.nx;
+  const size_t G = (size_t)p.ny * nx;
+  const int es = (p.storage == kBF16) ? 2 : 4;
+  const uint32_t round_bytes = (uint32_t)LPC * nx * es;
+  float2* lines = reinterpret_cast<float2*>(smraw);
+  unsigned char* stage = smraw + (((size_t)p.R * pitch * sizeof(float2) + 127) & ~(size_t)127);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + round_bytes);
+  int* flag = reinterpret_cast<int*>(bar + 1);
+  const long long Q = (long long)p.M * p.N * p.n_tiles;
+  char* ens = reinterpret_cast<char*>(p.ens);
+
+  auto issue = [&](long long q, int r) {      // forecast rows of the next round
+    const size_t f = q / p.n_tiles;
+    const int tile = (int)(q - (long long)f * p.n_tiles);
+    const size_t row0 = (size_t)tile * p.R + (size_t)r * LPC;
+    mbar_arrive_expect_tx(bar, round_bytes);
+    bulk_g2s(stage, ens + (f * G + row0 * nx) * es, round_bytes, bar);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
   }
   __syncthreads();
-  void* u = (p.storage == kBF16) ? (void*)((__nv_bfloat16*)p.ens + f * G) : (void*)((float*)p.ens + f * G);
-  for (int r0 = 0; r0 < p.R; r0 += LPC) {
-    const int r = r0 + g;
-    float2* line = sm + r * pitch;
-    float2 v[V];
-#pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const int c = t + T * m;
-      const float2 X = line[pidx(c)];
-      if (c == 0) {
-        v[m] = make_float2(X.x + X.y, X.x - X.y);
-      } else {
-        const float2 Xc = line[pidx(L - c)];
-        const float2 A = make_float2(X.x + Xc.x, X.y - Xc.y);
-        const float2 B = make_float2(X.x - Xc.x, X.y + Xc.y);
-        const float2 Bw = cmulc(B, __ldg(p.twX + c));
-        v[m] = make_float2(A.x - Bw.y, A.y + Bw.x);
+  uint32_t phase = 0;
+  long long q = blockIdx.x;
+  if (threadIdx.x == 0 && q < Q) issue(q, 0);
+  const int RP = p.R >> 1;
+  const int rp = threadIdx.x % RP;
+  const int cstep = blockDim.x / RP;
+  for (; q < Q; q += gridDim.x) {
+    const size_t f = q / p.n_tiles;               // field j*N + k
+    const int tile = (int)(q - (long long)f * p.n_tiles);
+    const int y0 = tile * p.R;
+    {
+      const float2* in = p.in + f * (size_t)L * p.ny + y0 + 2 * rp;
+      float2* s0 = lines + (2 * rp) * pitch;
+      float2* s1 = s0 + pitch;
+      for (int c = threadIdx.x / RP; c < L; c += cstep) {
+        const float4 v4 = __ldcs(reinterpret_cast<const float4*>(in + (size_t)c * p.ny));
+        s0[pidx(c)] = make_float2(v4.x, v4.y);
+        s1[pidx(c)] = make_float2(v4.z, v4.w);
       }
     }
     __syncthreads();
-    fft_line<L, V, true>(v, line, t, p.twL);
-    const size_t rowoff = (size_t)(y0 + r) * p.nx;
+    for (int r = 0; r < rounds; ++r) {
+      const int row = r * LPC + g;
+      float2* line = lines + row * pitch;
+      float2 v[V];
 #pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const size_t idx = rowoff + 2 * (size_t)(t + T * m);
-      const float2 a = load2(u, idx, p.storage);
-      store2(u, idx, make_float2(a.x + v[m].x, a.y + v[m].y), p.storage);
+      for (int m = 0; m < V; ++m) {
+        const int c = t + T * m;
+        const float2 X = line[pidx(c)];
+        if (c == 0) {
+          v[m] = make_float2(X.x + X.y, X.x - X.y);
+        } else {
+          const float2 Xc = line[pidx(L - c)];
+          const float2 A = make_float2(X.x + Xc.x, X.y - Xc.y);
+          const float2 B = make_float2(X.x - Xc.x, X.y + Xc.y);
+          const float2 Bw = cmulc(B, __ldg(p.twX + c));
+          v[m] = make_float2(A.x - Bw.y, A.y + Bw.x);
+        }
+      }
+      __syncthreads();
+      fft_line<L, V, true>(v, line, t, p.twL);
+      if (!cta_wait(bar, phase, p.status, flag)) return;
+      phase ^= 1;
+      const unsigned char* st_row = stage + (size_t)g * nx * es;
+      float2 a[V];
+#pragma unroll
+      for (int m = 0; m < V; ++m) a[m] = load2(st_row, 2 * (size_t)(t + T * m), p.storage);
+      __syncthreads();   // stage consumed
+      if (threadIdx.x == 0) {
+        if (r + 1 < rounds) issue(q, r + 1);
+        else if (q + gridDim.x < Q) issue(q + gridDim.x, 0);
+      }
+      char* urow = ens + (f * G + (size_t)(y0 + row) * nx) * es;
+#pragma unroll
+      for (int m = 0; m < V; ++m)
+        store2(urow, 2 * (size_t)(t + T * m), make_float2(a[m].x + v[m].x, a[m].y + v[m].y), p.storage);
     }
+    __syncthreads();
   }
 }
 
 // ----------------------------------------------------------------- launch
+int sm_count();
+
 struct RowShape {
   int T, R, LPC;
   size_t smem;
 };
 
-static RowShape row_shape(int L, int V, int ny) {
+// rows per tile R (a power of two dividing ny), rows per round LPC, and the
+// shared memory: R staged rows plus one round of n_in input rows
+static RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in) {
   RowShape s;
   s.T = L / V;
-  int pow2 = ny & -ny;                       // largest power of two dividing ny
+  const int pow2 = ny & -ny;
   int R = 256 / s.T;
   if (R < 8) R = 8;
   if (R > pow2) R = pow2;
-  while (R > 2 && (size_t)R * (padded_len(L) + 1) * sizeof(float2) > 160 * 1024) R >>= 1;
-  s.R = R;
-  int LPC = 512 / s.T;
-  if (LPC < 1) LPC = 1;
-  if (LPC > R) LPC = R;
-  s.LPC = LPC;
-  s.smem = (size_t)R * (padded_len(L) + 1) * sizeof(float2);
-  return s;
+  for (;;) {
+    int LPC = 512 / s.T;
+    if (LPC < 1) LPC = 1;
+    if (LPC > R) LPC = R;
+    const size_t lines = ((size_t)R * (padded_len(L) + 1) * sizeof(float2) + 127) & ~(size_t)127;
+    const size_t smem = lines + (size_t)n_in * LPC * nx * es + 16;
+    if (smem <= 220 * 1024 || R <= 2) {
+      s.R = R;
+      s.LPC = LPC;
+      s.smem = smem;
+      return s;
+    }
+    R >>= 1;
+  }
 }
 
 template <int L>
 static cudaError_t row_fwd_L(RowFwdParams p, int n_fields, cudaStream_t st) {
   constexpr int V = default_V(L);
-  RowShape s = row_shape(L, V, p.ny);
+  const int es = p.storage == kBF16 ? 2 : 4;
+  RowShape s = row_shape(L, V, p.ny, p.nx, es, p.mode == kAnomaly ? 1 : 2);
+  if (s.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   p.R = s.R;
   p.n_tiles = p.ny / s.R;
   auto kern = row_fwd_kernel<L, V>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
   if (e != cudaSuccess) return e;
-  const long long grid = (long long)n_fields * p.n_tiles;  // = (obs or blocks) * tiles * N
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.T * s.LPC, s.smem);
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)n_fields * p.n_tiles;
+  const long long cap = (long long)sm_count() * per_sm;
+  if (grid > cap) grid = cap;
   kern<<<(unsigned)grid, s.T * s.LPC, s.smem, st>>>(p);
   return cudaGetLastError();
 }
@@ -249,13 +353,20 @@ static cudaError_t row_fwd_L(RowFwdParams p, int n_fields, cudaStream_t st) {
 template <int L>
 static cudaError_t row_inv_L(RowInvParams p, int n_fields, cudaStream_t st) {
   constexpr int V = default_V(L);
-  RowShape s = row_shape(L, V, p.ny);
+  const int es = p.storage == kBF16 ? 2 : 4;
+  RowShape s = row_shape(L, V, p.ny, p.nx, es, 1);
+  if (s.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   p.R = s.R;
   p.n_tiles = p.ny / s.R;
   auto kern = row_inv_kernel<L, V>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
   if (e != cudaSuccess) return e;
-  const long long grid = (long long)n_fields * p.n_tiles;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.T * s.LPC, s.smem);
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)n_fields * p.n_tiles;
+  const long long cap = (long long)sm_count() * per_sm;
+  if (grid > cap) grid = cap;
   kern<<<(unsigned)grid, s.T * s.LPC, s.smem, st>>>(p);
   return cudaGetLastError();
 }
