@@ -63,9 +63,10 @@ struct fftenkf_plan_s {
   int used[kPassCount] = {};
   double acc_ms[kPassCount] = {};
   int launches[kPassCount] = {};
+  size_t off_twY = 0, off_twX = 0;
   const float2* twL() const { return d_tw; }
-  const float2* twY() const { return d_tw + L; }
-  const float2* twX() const { return d_tw + L + ny; }
+  const float2* twY() const { return d_tw + off_twY; }
+  const float2* twX() const { return d_tw + off_twX; }
 };
 
 // fold a completed slot into the totals
@@ -94,12 +95,27 @@ static void prof_end(fftenkf_plan p, int pass, cudaStream_t s) {
   p->used[pass] += 1;
 }
 
+static float2 unit_root(long long e, long long n) {   // exp(-2 pi i e / n), FP64 then rounded
+  const double ang = 2.0 * M_PI * (double)(e % n) / (double)n;
+  return make_float2((float)std::cos(ang), (float)-std::sin(ang));
+}
+
+// plain table exp(-2 pi i e / n), e < count
 static void host_twiddles(std::vector<float2>& out, int n, int count) {
-  for (int e = 0; e < count; ++e) {
-    const long long r = e % n;
-    const double ang = 2.0 * M_PI * (double)r / (double)n;
-    out.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
+  for (int e = 0; e < count; ++e) out.push_back(unit_root(e, n));
+}
+
+// stage-major table of the line FFT plan (n, default V), laid out as fft_core.cuh reads it
+static void host_stage_twiddles(std::vector<float2>& out, int n) {
+  const int V = default_V(n);
+  const int S = num_stages(n, V);
+  const size_t base = out.size();
+  for (int s = 1; s < S; ++s) {
+    const int R = radix_at(n, V, s), NS = stage_ns(n, V, s);
+    for (int r = 1; r < R; ++r)
+      for (int jm = 0; jm < NS; ++jm) out.push_back(unit_root((long long)jm * r * (n / (NS * R)), n));
   }
+  if (out.size() - base != (size_t)twiddle_count(n, V)) out.resize(base + twiddle_count(n, V));
 }
 
 extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_dims* dims,
@@ -158,9 +174,12 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
   p->ws_bytes = off;
   cudaGetDevice(&p->device);
   std::vector<float2> tw;
-  host_twiddles(tw, p->L, p->L);
-  host_twiddles(tw, p->ny, p->ny);
+  host_stage_twiddles(tw, p->L);
+  p->off_twY = tw.size();
+  host_stage_twiddles(tw, p->ny);
+  p->off_twX = tw.size();
   host_twiddles(tw, p->nx, p->L + 1);
+  if (tw.size() % 2) tw.push_back(make_float2(0.f, 0.f));
   cudaError_t e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
   if (e != cudaSuccess) {
     delete p;

@@ -176,6 +176,22 @@ template <bool INV> struct Dft<16, INV> {
   }
 };
 
+// Twiddle tables: for every stage s with NS > 1 the factors
+// W_N^((j mod NS) r N/(NS R)) are stored as rows r = 1..R-1 of NS entries, so
+// the threads of a warp (consecutive j) read consecutive entries.  Stages are
+// concatenated in order; twiddle_offset(N, V, s) is where stage s starts.
+__host__ __device__ constexpr int stage_ns(int N, int V, int s) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= radix_at(N, V, i);
+  return ns;
+}
+__host__ __device__ constexpr int twiddle_offset(int N, int V, int s) {
+  int off = 0;
+  for (int i = 1; i < s; ++i) off += (radix_at(N, V, i) - 1) * stage_ns(N, V, i);
+  return off;
+}
+__host__ __device__ constexpr int twiddle_count(int N, int V) { return twiddle_offset(N, V, num_stages(N, V)); }
+
 // ------------------------------------------------------------------ stages
 // Stage S of the Stockham transform; NS = product of the radices before it.
 // Butterfly j reads x[j + r N/R], multiplies by W_N^((j mod NS) r N/(NS R)),
@@ -196,10 +212,10 @@ struct Stage {
       for (int r = 0; r < R; ++r) a[r] = v[b + r * B];
       const int j = t + T * b;
       if (NS > 1) {
-        const int step = (j % NS) * (N / (NS * R));
+        const float2* tws = tw + twiddle_offset(N, V, S) + (j % NS);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(tw + step * r);
+          float2 w = __ldg(tws + (r - 1) * NS);
           if (INV) w.y = -w.y;
           a[r] = cmul(a[r], w);
         }
@@ -226,7 +242,8 @@ struct Stage {
 
 // Unnormalised line DFT, sign -1 (forward) or +1 (INV).  Every thread of the
 // CTA must call it (it contains __syncthreads when the plan has >1 stage).
-// tw[e] = exp(-2 pi i e / N), e < N.  sm: this line's padded buffer.
+// tw: the stage-major twiddle table of (N, V) described above (exp(-2 pi i e/N)
+// values).  sm: this line's padded buffer.
 template <int N, int V, bool INV>
 __device__ __forceinline__ void fft_line(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
   static_assert(N % V == 0, "V must divide N");

@@ -260,13 +260,17 @@ __global__ void __launch_bounds__(256, 1) col_update_kernel(const ColUpdParams p
     const int part = (c == 0) ? 1 : ((c == p.L) ? 2 : 0);
     float2* w = wst + s * stage_elems + (size_t)g * p.n_obs * NY;
     const float2* gl = gst + (size_t)g * p.n_obs * NY;
-    // forward column transforms of the innovations, kept in place in the stage
-    for (int i = 0; i < p.n_obs; ++i) {
-      float2 v[V];
-      read_line<NY, V>(v, w + (size_t)i * NY, t, part);
-      fft_line<NY, V, false>(v, xbuf, t, p.twY);
+    // forward column transforms of the innovations, kept in registers
+    float2 wv[NOBS][V];
 #pragma unroll
-      for (int m = 0; m < V; ++m) w[(size_t)i * NY + t + T * m] = v[m];
+    for (int i = 0; i < NOBS; ++i) {
+      if (i < p.n_obs) {
+        read_line<NY, V>(wv[i], w + (size_t)i * NY, t, part);
+        fft_line<NY, V, false>(wv[i], xbuf, t, p.twY);
+      } else {
+#pragma unroll
+        for (int m = 0; m < V; ++m) wv[i][m] = make_float2(0.f, 0.f);
+      }
     }
     for (int j = 0; j < p.M; ++j) {
       if (!cta_wait(gbar, gph, p.status, flag)) {
@@ -279,23 +283,28 @@ __global__ void __launch_bounds__(256, 1) col_update_kernel(const ColUpdParams p
       gph ^= 1;
       float2 sv[V];
       const int io = p.obs_of_block[j];
+#pragma unroll
+      for (int m = 0; m < V; ++m) sv[m] = make_float2(0.f, 0.f);
       if (io >= 0) {
         const float* gp = reinterpret_cast<const float*>(gl) + t;
-        const float2* wp = w + (size_t)io * NY + t;
 #pragma unroll
-        for (int m = 0; m < V; ++m) {
-          const float gv = gp[T * m];
-          const float2 x = wp[T * m];
-          sv[m] = make_float2(gv * x.x, gv * x.y);
+        for (int i = 0; i < NOBS; ++i) {
+          if (i == io) {
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+              const float gv = gp[T * m];
+              sv[m] = make_float2(gv * wv[i][m].x, gv * wv[i][m].y);
+            }
+          }
         }
       } else {
 #pragma unroll
-        for (int m = 0; m < V; ++m) sv[m] = make_float2(0.f, 0.f);
-        for (int i = 0; i < p.n_obs; ++i) {
-          const float2* gp = gl + (size_t)i * NY + t;
-          const float2* wp = w + (size_t)i * NY + t;
+        for (int i = 0; i < NOBS; ++i) {
+          if (i < p.n_obs) {
+            const float2* gp = gl + (size_t)i * NY + t;
 #pragma unroll
-          for (int m = 0; m < V; ++m) sv[m] = cadd(sv[m], cmul(gp[T * m], wp[T * m]));
+            for (int m = 0; m < V; ++m) sv[m] = cadd(sv[m], cmul(gp[T * m], wv[i][m]));
+          }
         }
       }
       __syncthreads();   // gain stage consumed
