@@ -126,6 +126,18 @@ fftenkf_status fftenkf_pass_times(fftenkf_plan plan, double* total_ms, int* laun
 int fftenkf_pass_count(void);
 const char* fftenkf_pass_name(int pass);
 
+/* Line-FFT schedule per pass (indexed like fftenkf_pass_name; passes without
+ * transforms ignore theirs): 0 = wide plan (radix-16 stages, 16 values per
+ * thread; radix 8/3 with 24 values for 3*2^a lengths), 1 = narrow plan (radix-8
+ * stages, 8 values per thread, twice the threads per line).  Row passes take
+ * a second bit (value 2 or 3): half as many rows per tile, so that two CTAs fit
+ * on one SM.  set returns EINVAL for out-of-range entries and EUNSUPPORTED if a
+ * choice does not fit
+ * in shared memory; the plan keeps its previous schedule then.  The schedule
+ * changes speed only: every schedule computes the same analysis. */
+fftenkf_status fftenkf_set_schedule(fftenkf_plan plan, const int* sched, int n);
+fftenkf_status fftenkf_get_schedule(fftenkf_plan plan, int* sched, int n);
+
 /* Static description of a status code. */
 const char* fftenkf_status_string(fftenkf_status s);
 /* Message of the last failing call on this host thread ("" if none). */

@@ -49,6 +49,8 @@ _SIGNATURES = [
     ("fftenkf_pass_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_pass_count", ctypes.c_int, []),
+    ("fftenkf_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("fftenkf_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_pass_name", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_last_error", ctypes.c_char_p, []),
@@ -154,3 +156,15 @@ def fftenkf_pass_times(plan):
     cnt = (ctypes.c_int * n)()
     check(lib().fftenkf_pass_times(plan, ms, cnt, n), "fftenkf_pass_times")
     return {fftenkf_pass_name(i): (ms[i], cnt[i]) for i in range(n)}
+
+
+def fftenkf_set_schedule(plan, sched):
+    arr = (ctypes.c_int * len(sched))(*[int(x) for x in sched])
+    check(lib().fftenkf_set_schedule(plan, arr, len(sched)), "fftenkf_set_schedule")
+
+
+def fftenkf_get_schedule(plan):
+    n = fftenkf_pass_count()
+    arr = (ctypes.c_int * n)()
+    check(lib().fftenkf_get_schedule(plan, arr, n), "fftenkf_get_schedule")
+    return list(arr)

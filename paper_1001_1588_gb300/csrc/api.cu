@@ -63,9 +63,10 @@ struct fftenkf_plan_s {
   int used[kPassCount] = {};
   double acc_ms[kPassCount] = {};
   int launches[kPassCount] = {};
-  size_t off_twY = 0, off_twX = 0;
-  const float2* twL() const { return d_tw; }
-  const float2* twY() const { return d_tw + off_twY; }
+  size_t off_twL[2] = {0, 0}, off_twY[2] = {0, 0}, off_twX = 0;
+  int sched[kPassCount] = {};   // line-FFT schedule (plan_V selector) per pass
+  const float2* twL(int sel) const { return d_tw + off_twL[sel]; }
+  const float2* twY(int sel) const { return d_tw + off_twY[sel]; }
   const float2* twX() const { return d_tw + off_twX; }
 };
 
@@ -106,8 +107,7 @@ static void host_twiddles(std::vector<float2>& out, int n, int count) {
 }
 
 // stage-major table of the line FFT plan (n, default V), laid out as fft_core.cuh reads it
-static void host_stage_twiddles(std::vector<float2>& out, int n) {
-  const int V = default_V(n);
+static void host_stage_twiddles(std::vector<float2>& out, int n, int V) {
   const int S = num_stages(n, V);
   const size_t base = out.size();
   for (int s = 1; s < S; ++s) {
@@ -156,7 +156,7 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
     }
   }
   const int nf = p->n_obs + 2 * p->n_obs * p->n_un;
-  if (p->n_obs > 0 && (col_stats_smem(p->ny, nf, nullptr) == 0 || col_update_smem(p->ny, p->n_obs, nullptr, nullptr) == 0)) {
+  if (p->n_obs > 0 && (col_stats_smem(p->ny, nf, 0, nullptr) == 0 || col_update_smem(p->ny, p->n_obs, 0, nullptr, nullptr) == 0)) {
     delete p;
     return fail(FFTENKF_EUNSUPPORTED, "covariance tables per column exceed shared memory (reduce blocks or ny)");
   }
@@ -174,9 +174,12 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
   p->ws_bytes = off;
   cudaGetDevice(&p->device);
   std::vector<float2> tw;
-  host_stage_twiddles(tw, p->L);
-  p->off_twY = tw.size();
-  host_stage_twiddles(tw, p->ny);
+  for (int sel = 0; sel < 2; ++sel) {
+    p->off_twL[sel] = tw.size();
+    host_stage_twiddles(tw, p->L, plan_V(p->L, sel));
+    p->off_twY[sel] = tw.size();
+    host_stage_twiddles(tw, p->ny, plan_V(p->ny, sel));
+  }
   p->off_twX = tw.size();
   host_twiddles(tw, p->nx, p->L + 1);
   if (tw.size() % 2) tw.push_back(make_float2(0.f, 0.f));
@@ -264,7 +267,8 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   rp.n_obs = p->n_obs; rp.mode = kAnomaly; rp.storage = p->storage;
   rp.ens = ens; rp.mean = mp.mean;
   rp.out = reinterpret_cast<float2*>(ws + p->off_A);
-  rp.twL = p->twL(); rp.twX = p->twX(); rp.status = p->d_status;
+  rp.vsel = p->sched[kPassRowAnom];
+  rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
   prof_begin(p, kPassRowAnom, s);
   e = launch_row_fwd(rp, p->M * p->N, s);
   prof_end(p, kPassRowAnom, s);
@@ -277,7 +281,8 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   cp.A = rp.out;
   cp.chat = reinterpret_cast<float*>(ws + p->off_chat);
   cp.scale = (float)(1.0 / ((double)(p->N - 1) * (double)p->ny * (double)p->nx));
-  cp.twY = p->twY();
+  cp.vsel = p->sched[kPassStats];
+  cp.twY = p->twY(cp.vsel);
   cp.status = p->d_status;
   prof_begin(p, kPassStats, s);
   e = launch_col_stats(cp, s);
@@ -343,7 +348,8 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   for (int i = 0; i < p->n_obs; ++i) rp.obs[i] = p->obs[i];
   rp.ens = ensemble; rp.data = data; rp.pert = perturbations;
   rp.out = reinterpret_cast<float2*>(ws + p->off_W);
-  rp.twL = p->twL(); rp.twX = p->twX(); rp.status = p->d_status;
+  rp.vsel = p->sched[kPassRowInnov];
+  rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
   prof_begin(p, kPassRowInnov, s);
   if (e == cudaSuccess) e = launch_row_fwd(rp, p->N * p->n_obs, s);
   prof_end(p, kPassRowInnov, s);
@@ -357,14 +363,16 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   }
   up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
-  up.twY = p->twY(); up.status = p->d_status;
+  up.vsel = p->sched[kPassUpdate];
+  up.twY = p->twY(up.vsel); up.status = p->d_status;
   prof_begin(p, kPassUpdate, s);
   if (e == cudaSuccess) e = launch_col_update(up, s);
   prof_end(p, kPassUpdate, s);
   RowInvParams ip;
   memset(&ip, 0, sizeof(ip));
   ip.ny = p->ny; ip.nx = p->nx; ip.L = p->L; ip.M = p->M; ip.N = p->N; ip.storage = p->storage;
-  ip.in = up.S; ip.ens = ensemble; ip.twL = p->twL(); ip.twX = p->twX(); ip.status = p->d_status;
+  ip.vsel = p->sched[kPassRowInv];
+  ip.in = up.S; ip.ens = ensemble; ip.twL = p->twL(ip.vsel & 1); ip.twX = p->twX(); ip.status = p->d_status;
   prof_begin(p, kPassRowInv, s);
   if (e == cudaSuccess) e = launch_row_inv(ip, p->M * p->N, s);
   prof_end(p, kPassRowInv, s);
@@ -433,4 +441,26 @@ extern "C" int fftenkf_pass_count(void) { return kPassCount; }
 
 extern "C" const char* fftenkf_pass_name(int pass) {
   return (pass >= 0 && pass < kPassCount) ? kPassNames[pass] : "";
+}
+
+extern "C" fftenkf_status fftenkf_set_schedule(fftenkf_plan p, const int* sched, int n) {
+  if (!p || !sched || n < 0) return fail(FFTENKF_EINVAL, "null argument");
+  const int nf = p->n_obs + 2 * p->n_obs * p->n_un;
+  int next[kPassCount];
+  for (int a = 0; a < kPassCount; ++a) next[a] = (a < n) ? sched[a] : p->sched[a];
+  for (int a = 0; a < kPassCount; ++a) {
+    const bool row_pass = (a == kPassRowAnom || a == kPassRowInnov || a == kPassRowInv);
+    if (next[a] < 0 || next[a] > (row_pass ? 3 : 1)) return fail(FFTENKF_EINVAL, "schedule entry out of range");
+  }
+  if (p->n_obs > 0 && (col_stats_smem(p->ny, nf, next[kPassStats], nullptr) == 0 ||
+                       col_update_smem(p->ny, p->n_obs, next[kPassUpdate], nullptr, nullptr) == 0))
+    return fail(FFTENKF_EUNSUPPORTED, "schedule does not fit in shared memory");
+  for (int a = 0; a < kPassCount; ++a) p->sched[a] = next[a];
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_get_schedule(fftenkf_plan p, int* sched, int n) {
+  if (!p || !sched) return fail(FFTENKF_EINVAL, "null argument");
+  for (int a = 0; a < kPassCount && a < n; ++a) sched[a] = p->sched[a];
+  return FFTENKF_OK;
 }

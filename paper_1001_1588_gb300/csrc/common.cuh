@@ -66,6 +66,7 @@ struct RowFwdParams {
   const float2* twL;      // exp(-2 pi i e / L), e < L
   const float2* twX;      // exp(-2 pi i k / nx), k <= L
   int* status;
+  int vsel;               // line-FFT schedule (plan_V)
 };
 
 struct RowInvParams {
@@ -75,6 +76,7 @@ struct RowInvParams {
   const float2* twL;
   const float2* twX;
   int* status;
+  int vsel;
 };
 
 struct ColStatsParams {
@@ -84,8 +86,9 @@ struct ColStatsParams {
   const float2* A;        // anomaly row spectra, field j*N+k
   float* chat;            // [n_obs][L+1][ny] real, then [n_obs*n_un][L+1][ny] float2
   float scale;            // 1 / ((N-1) * ny * nx)
-  const float2* twY;      // exp(-2 pi i e / ny)
+  const float2* twY;      // stage-major twiddles of the ny-point plan
   int* status;
+  int vsel;
 };
 
 struct ColUpdParams {
@@ -99,6 +102,7 @@ struct ColUpdParams {
   const float2* twY;
   int* status;
   int n_stages;           // innovation prefetch stages (set by the launcher)
+  int vsel;
 };
 
 struct GainParams {
@@ -124,7 +128,7 @@ cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, int
 bool line_supported(int n);       // column line lengths
 bool row_line_supported(int n);   // row line lengths (nx/2)
 // shared-memory bytes a pass needs (0 = unsupported), for plan-time checks
-size_t col_stats_smem(int ny, int nf, int* lpc);
-size_t col_update_smem(int ny, int n_obs, int* lpc, int* n_stages);
+size_t col_stats_smem(int ny, int nf, int vsel, int* lpc);
+size_t col_update_smem(int ny, int n_obs, int vsel, int* lpc, int* n_stages);
 
 }  // namespace fftenkf

@@ -60,10 +60,18 @@ __host__ __device__ constexpr int num_stages(int N, int V) {
 __host__ __device__ constexpr int default_V(int N) {
   return (N % 3 == 0) ? (N >= 24 ? 24 : N) : (N >= 16 ? 16 : N);
 }
+// values per thread of schedule `sel`: 0 = wide (radix 16 / 8-3), 1 = narrow (radix 8 / 4-3):
+// twice the threads per line, one more exchange
+__host__ __device__ constexpr int plan_V(int N, int sel) {
+  return sel == 0 ? default_V(N) : ((N % 3 == 0) ? (N >= 12 ? 12 : N) : (N >= 8 ? 8 : N));
+}
 // padded shared-memory index: one spare slot per 16 keeps stride-R writes
 // of the Stockham stages on distinct 8-byte banks
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
+// pitch of the staged rows of the row passes: a padded line rounded to 2 (mod 8) slots, so
+// that reading two rows x four columns per half-warp hits 16 distinct 8-byte banks
+__host__ __device__ constexpr int row_pitch(int N) { return padded_len(N) + ((10 - padded_len(N) % 8) % 8); }
 
 // ------------------------------------------------------------------ small DFTs
 // Forward kernels use exp(-2 pi i / R); INV uses exp(+2 pi i / R).

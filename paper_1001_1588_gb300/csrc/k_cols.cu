@@ -18,8 +18,8 @@ int sm_count() {
 static size_t padded_bytes(int ny) { return (size_t)((padded_len(ny) + 1) & ~1) * sizeof(float2); }
 
 // per group: accumulators nf*ny floats, exchange line, one prefetch line
-size_t col_stats_smem(int ny, int nf, int* lpc) {
-  const int V = default_V(ny);
+size_t col_stats_smem(int ny, int nf, int vsel, int* lpc) {
+  const int V = plan_V(ny, vsel);
   const int T = ny / V;
   const size_t per = (size_t)nf * ny * sizeof(float) + padded_bytes(ny) + (size_t)ny * sizeof(float2);
   int n = 256 / T;
@@ -31,8 +31,8 @@ size_t col_stats_smem(int ny, int nf, int* lpc) {
 }
 
 // per group: one or two stages of n_obs innovation lines, one stage of gain lines, exchange line
-size_t col_update_smem(int ny, int n_obs, int* lpc, int* n_stages) {
-  const int V = default_V(ny);
+size_t col_update_smem(int ny, int n_obs, int vsel, int* lpc, int* n_stages) {
+  const int V = plan_V(ny, vsel);
   const int T = ny / V;
   const size_t lines = (size_t)n_obs * ny * sizeof(float2);
   for (int nst = 2; nst >= 1; --nst) {

@@ -37,7 +37,7 @@ __device__ __forceinline__ void read_line(float2 (&v)[V], const float2* __restri
 // ----------------------------------------------------------------- col_stats
 // smem: acc [LPC][nf][NY] f32 | xbuf [LPC][padded(NY)] f2 | stage [LPC][NY] f2 | bar | flag
 template <int NY, int V, int NOBS>
-__global__ void __launch_bounds__(256, 1) col_stats_kernel(const ColStatsParams p) {
+__global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kernel(const ColStatsParams p) {
   constexpr int T = NY / V;
   extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256, 1) col_stats_kernel(const ColStatsParams 
 // stage, read into registers before the next copy is issued).
 // smem: wst [nst][LPC][n_obs][NY] f2 | gst [LPC][n_obs][NY] f2 | xbuf [LPC][PL] f2 | bars[3] | flag
 template <int NY, int V, int NOBS>
-__global__ void __launch_bounds__(256, 1) col_update_kernel(const ColUpdParams p) {
+__global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kernel(const ColUpdParams p) {
   constexpr int T = NY / V;
   constexpr int PL = (padded_len(NY) + 1) & ~1;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -333,13 +333,12 @@ __global__ void __launch_bounds__(256, 1) col_update_kernel(const ColUpdParams p
 // ----------------------------------------------------------------- launch templates
 int sm_count();
 
-template <int NY, int NOBS>
-inline cudaError_t col_stats_NY(const ColStatsParams& p, cudaStream_t st) {
-  constexpr int V = default_V(NY);
+template <int NY, int V, int NOBS>
+inline cudaError_t col_stats_NYV(const ColStatsParams& p, cudaStream_t st) {
   constexpr int T = NY / V;
   int lpc = 1;
   const int nf = p.n_obs + 2 * p.n_obs * p.n_un;
-  const size_t smem = col_stats_smem(NY, nf, &lpc);
+  const size_t smem = col_stats_smem(NY, nf, p.vsel, &lpc);
   if (smem == 0) return cudaErrorInvalidConfiguration;
   auto kern = col_stats_kernel<NY, V, NOBS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -356,12 +355,11 @@ inline cudaError_t col_stats_NY(const ColStatsParams& p, cudaStream_t st) {
 
 size_t col_update_smem(int ny, int n_obs, int* lpc, int* n_stages);
 
-template <int NY, int NOBS>
-inline cudaError_t col_update_NY(const ColUpdParams& p, cudaStream_t st) {
-  constexpr int V = default_V(NY);
+template <int NY, int V, int NOBS>
+inline cudaError_t col_update_NYV(const ColUpdParams& p, cudaStream_t st) {
   constexpr int T = NY / V;
   int lpc = 1, nst = 2;
-  const size_t smem = col_update_smem(NY, p.n_obs, &lpc, &nst);
+  const size_t smem = col_update_smem(NY, p.n_obs, p.vsel, &lpc, &nst);
   if (smem == 0) return cudaErrorInvalidConfiguration;
   ColUpdParams q = p;
   q.n_stages = nst;
@@ -377,6 +375,18 @@ inline cudaError_t col_update_NY(const ColUpdParams& p, cudaStream_t st) {
   if (grid > groups) grid = groups;
   kern<<<(unsigned)grid, T * lpc, smem, st>>>(q);
   return cudaGetLastError();
+}
+
+template <int NY, int NOBS>
+inline cudaError_t col_stats_NY(const ColStatsParams& p, cudaStream_t st) {
+  if (p.vsel) return col_stats_NYV<NY, plan_V(NY, 1), NOBS>(p, st);
+  return col_stats_NYV<NY, plan_V(NY, 0), NOBS>(p, st);
+}
+
+template <int NY, int NOBS>
+inline cudaError_t col_update_NY(const ColUpdParams& p, cudaStream_t st) {
+  if (p.vsel) return col_update_NYV<NY, plan_V(NY, 1), NOBS>(p, st);
+  return col_update_NYV<NY, plan_V(NY, 0), NOBS>(p, st);
 }
 
 #define FFTENKF_COL_SIZES(X) \

@@ -15,6 +15,19 @@ namespace fftenkf {
 
 constexpr int TB = 32;
 
+// 1/x in FP64 for normal x > 0: the hardware's approximate reciprocal refined
+// by two steps of the Newton-Raphson iteration for f(y) = 1/y - x
+// (e <- 1 - x y, y <- y + y e), each of which doubles the correct bits.
+// Subnormal or zero x are handled by the caller.
+__device__ __forceinline__ double recip64(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // load a [ny][L+1] double tile (rows ky0.., cols c0..) into s[ky][c]
 __device__ __forceinline__ void load_tile(double (*s)[TB + 1], const double* __restrict__ src, int ny, int L1,
                                           int ky0, int c0, int stride_elems, int comp) {
@@ -49,8 +62,9 @@ __global__ void __launch_bounds__(256) gain_kernel(const GainParams p) {
       const double a = p.spec ? ca[threadIdx.x][cl] : (double)p.chat_t[i * tab + (size_t)c * p.ny + ky];
       bad |= !isfinite(a);
       const double den = a + rs[threadIdx.x][cl];
-      inv[q] = (den != 0.0) ? 1.0 / den : 0.0;
-      p.goo[i * tab + (size_t)c * p.ny + ky] = (float)(a * inv[q] * (double)p.scale);
+      inv[q] = (den > 1e-300) ? recip64(den) : ((den != 0.0) ? 1.0 / den : 0.0);
+      inv[q] *= (double)p.scale;
+      p.goo[i * tab + (size_t)c * p.ny + ky] = (float)(a * inv[q]);
     }
   }
   const double* xspec = p.spec ? p.spec + (size_t)p.n_obs * K : nullptr;
@@ -78,7 +92,7 @@ __global__ void __launch_bounds__(256) gain_kernel(const GainParams p) {
           im = v.y;
         }
         bad |= !(isfinite(re) && isfinite(im));
-        const double sc = inv[q] * (double)p.scale;
+        const double sc = inv[q];
         p.gjo[qt * tab + (size_t)c * p.ny + ky] = make_float2((float)(re * sc), (float)(im * sc));
       }
     }

@@ -96,7 +96,7 @@ __device__ __forceinline__ RowTile decode_tile(long long q, int N, int n_tiles) 
 template <int L, int V>
 __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   constexpr int T = L / V;
-  constexpr int pitch = padded_len(L) + 1;
+  constexpr int pitch = row_pitch(L);
   extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
   const int rounds = p.R / LPC;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
 template <int L, int V>
 __global__ void __launch_bounds__(512, 1) row_inv_kernel(const RowInvParams p) {
   constexpr int T = L / V;
-  constexpr int pitch = padded_len(L) + 1;
+  constexpr int pitch = row_pitch(L);
   extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
   const int rounds = p.R / LPC;
@@ -249,10 +249,24 @@ __global__ void __launch_bounds__(512, 1) row_inv_kernel(const RowInvParams p) {
       const float2* in = p.in + f * (size_t)L * p.ny + y0 + 2 * rp;
       float2* s0 = lines + (2 * rp) * pitch;
       float2* s1 = s0 + pitch;
-      for (int c = threadIdx.x / RP; c < L; c += cstep) {
-        const float4 v4 = __ldcs(reinterpret_cast<const float4*>(in + (size_t)c * p.ny));
-        s0[pidx(c)] = make_float2(v4.x, v4.y);
-        s1[pidx(c)] = make_float2(v4.z, v4.w);
+      // 8 loads in flight per thread before their values are staged
+      const int c0 = threadIdx.x / RP;
+      const int nper = (L + cstep - 1) / cstep;
+      for (int i0 = 0; i0 < nper; i0 += 8) {
+        float4 v4[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + (i0 + u) * cstep;
+          if (i0 + u < nper && c < L) v4[u] = __ldcs(reinterpret_cast<const float4*>(in + (size_t)c * p.ny));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + (i0 + u) * cstep;
+          if (i0 + u < nper && c < L) {
+            s0[pidx(c)] = make_float2(v4[u].x, v4[u].y);
+            s1[pidx(c)] = make_float2(v4[u].z, v4[u].w);
+          }
+        }
       }
     }
     __syncthreads();
@@ -306,18 +320,19 @@ struct RowShape {
 
 // rows per tile R (a power of two dividing ny), rows per round LPC, and the
 // shared memory: R staged rows plus one round of n_in input rows
-static RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in) {
+static RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in, bool half) {
   RowShape s;
   s.T = L / V;
   const int pow2 = ny & -ny;
   int R = 256 / s.T;
   if (R < 8) R = 8;
   if (R > pow2) R = pow2;
+  if (half && R > 2) R >>= 1;
   for (;;) {
     int LPC = 512 / s.T;
     if (LPC < 1) LPC = 1;
     if (LPC > R) LPC = R;
-    const size_t lines = ((size_t)R * (padded_len(L) + 1) * sizeof(float2) + 127) & ~(size_t)127;
+    const size_t lines = ((size_t)R * row_pitch(L) * sizeof(float2) + 127) & ~(size_t)127;
     const size_t smem = lines + (size_t)n_in * LPC * nx * es + 16;
     if (smem <= 220 * 1024 || R <= 2) {
       s.R = R;
@@ -329,11 +344,10 @@ static RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in) {
   }
 }
 
-template <int L>
-static cudaError_t row_fwd_L(RowFwdParams p, int n_fields, cudaStream_t st) {
-  constexpr int V = default_V(L);
+template <int L, int V>
+static cudaError_t row_fwd_LV(RowFwdParams p, int n_fields, cudaStream_t st) {
   const int es = p.storage == kBF16 ? 2 : 4;
-  RowShape s = row_shape(L, V, p.ny, p.nx, es, p.mode == kAnomaly ? 1 : 2);
+  RowShape s = row_shape(L, V, p.ny, p.nx, es, p.mode == kAnomaly ? 1 : 2, (p.vsel & 2) != 0);
   if (s.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   p.R = s.R;
   p.n_tiles = p.ny / s.R;
@@ -350,11 +364,10 @@ static cudaError_t row_fwd_L(RowFwdParams p, int n_fields, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int L>
-static cudaError_t row_inv_L(RowInvParams p, int n_fields, cudaStream_t st) {
-  constexpr int V = default_V(L);
+template <int L, int V>
+static cudaError_t row_inv_LV(RowInvParams p, int n_fields, cudaStream_t st) {
   const int es = p.storage == kBF16 ? 2 : 4;
-  RowShape s = row_shape(L, V, p.ny, p.nx, es, 1);
+  RowShape s = row_shape(L, V, p.ny, p.nx, es, 1, (p.vsel & 2) != 0);
   if (s.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   p.R = s.R;
   p.n_tiles = p.ny / s.R;
@@ -369,6 +382,18 @@ static cudaError_t row_inv_L(RowInvParams p, int n_fields, cudaStream_t st) {
   if (grid > cap) grid = cap;
   kern<<<(unsigned)grid, s.T * s.LPC, s.smem, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t row_fwd_L(const RowFwdParams& p, int n_fields, cudaStream_t st) {
+  if (p.vsel & 1) return row_fwd_LV<L, plan_V(L, 1)>(p, n_fields, st);
+  return row_fwd_LV<L, plan_V(L, 0)>(p, n_fields, st);
+}
+
+template <int L>
+static cudaError_t row_inv_L(const RowInvParams& p, int n_fields, cudaStream_t st) {
+  if (p.vsel & 1) return row_inv_LV<L, plan_V(L, 1)>(p, n_fields, st);
+  return row_inv_LV<L, plan_V(L, 0)>(p, n_fields, st);
 }
 
 #define FFTENKF_ROW_SIZES(X) \
