@@ -138,6 +138,33 @@ const char* fftenkf_pass_name(int pass);
 fftenkf_status fftenkf_set_schedule(fftenkf_plan plan, const int* sched, int n);
 fftenkf_status fftenkf_get_schedule(fftenkf_plan plan, int* sched, int n);
 
+/* ---------------------------------------------------------------- batched
+ * Many independent analyses of uneven sizes (the block-state method with one
+ * fully observed block each, H = I, eq. spectral-enkf): every pass is one
+ * persistent launch over a work list mixing the units of all analyses, and
+ * the seven launches are replayed as one CUDA graph (captured on the first
+ * call and after every autotune).  dims[i].n_blocks must be 1; all analyses
+ * share one storage type; ny and nx/2 in {2^a, 3*2^a} between 16 and 1024.
+ * The pointer arguments of fftenkf_analyze_batched are HOST arrays of `count`
+ * DEVICE pointers with the single-analysis layouts (ensemble [N][ny][nx],
+ * data [ny][nx] float, perturbations [N][ny][nx], rhat [ny][nx/2+1] double). */
+typedef struct fftenkf_batch_s* fftenkf_batch;
+fftenkf_status fftenkf_plan_batched(fftenkf_batch* batch, int count, const fftenkf_dims* dims);
+fftenkf_status fftenkf_batch_destroy(fftenkf_batch batch);
+fftenkf_status fftenkf_batch_workspace_size(fftenkf_batch batch, size_t* bytes);
+fftenkf_status fftenkf_analyze_batched(fftenkf_batch batch, void* const* ensembles, const float* const* data,
+                                       const void* const* perturbations, const double* const* rhat,
+                                       void* workspace, void* stream);
+/* Autotuner: times every candidate CTA size (128, 256 threads) and line-FFT
+ * schedule (0, 1) of every pass on zero-filled scratch inputs of the batch's
+ * shapes (allocated for the call: one copy of every item's inputs) and keeps
+ * the fastest; best_ms (may be NULL) receives the sum of the best pass times. */
+fftenkf_status fftenkf_batch_autotune(fftenkf_batch batch, void* workspace, void* stream, double* best_ms);
+/* Chosen CTA size and schedule of each batched pass (7 passes: mean, anomaly
+ * rows, statistics, gain, innovation rows, update, inverse rows). */
+fftenkf_status fftenkf_batch_schedule(fftenkf_batch batch, int* cta_threads, int* sched, int n);
+fftenkf_status fftenkf_batch_last_device_status(fftenkf_batch batch, void* stream);
+
 /* Static description of a status code. */
 const char* fftenkf_status_string(fftenkf_status s);
 /* Message of the last failing call on this host thread ("" if none). */

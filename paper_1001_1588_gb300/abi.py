@@ -52,6 +52,15 @@ _SIGNATURES = [
     ("fftenkf_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_pass_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("fftenkf_plan_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(fftenkf_dims)]),
+    ("fftenkf_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("fftenkf_batch_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("fftenkf_analyze_batched", ctypes.c_int, [ctypes.c_void_p] * 7),
+    ("fftenkf_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_double)]),
+    ("fftenkf_batch_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("fftenkf_batch_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("fftenkf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_last_error", ctypes.c_char_p, []),
 ]
@@ -168,3 +177,48 @@ def fftenkf_get_schedule(plan):
     arr = (ctypes.c_int * n)()
     check(lib().fftenkf_get_schedule(plan, arr, n), "fftenkf_get_schedule")
     return list(arr)
+
+
+# ---------------------------------------------------------------- batched
+def fftenkf_plan_batched(dims, storage):
+    """dims: sequence of (ny, nx, n_members); one observed block each."""
+    arr = (fftenkf_dims * len(dims))(*[fftenkf_dims(ny, nx, 1, n, storage) for ny, nx, n in dims])
+    b = ctypes.c_void_p()
+    check(lib().fftenkf_plan_batched(ctypes.byref(b), len(dims), arr), "fftenkf_plan_batched")
+    return b.value
+
+
+def fftenkf_batch_destroy(b):
+    check(lib().fftenkf_batch_destroy(b), "fftenkf_batch_destroy")
+
+
+def fftenkf_batch_workspace_size(b) -> int:
+    n = ctypes.c_size_t()
+    check(lib().fftenkf_batch_workspace_size(b, ctypes.byref(n)), "fftenkf_batch_workspace_size")
+    return n.value
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[_p(x) for x in xs])
+
+
+def fftenkf_analyze_batched(b, ensembles, data, perturbations, rhat, workspace=None, stream=None):
+    check(lib().fftenkf_analyze_batched(b, _ptr_array(ensembles), _ptr_array(data), _ptr_array(perturbations),
+                                        _ptr_array(rhat), _p(workspace), stream), "fftenkf_analyze_batched")
+
+
+def fftenkf_batch_autotune(b, workspace=None, stream=None) -> float:
+    ms = ctypes.c_double()
+    check(lib().fftenkf_batch_autotune(b, _p(workspace), stream, ctypes.byref(ms)), "fftenkf_batch_autotune")
+    return ms.value
+
+
+def fftenkf_batch_schedule(b, n=7):
+    bt = (ctypes.c_int * n)()
+    sc = (ctypes.c_int * n)()
+    check(lib().fftenkf_batch_schedule(b, bt, sc, n), "fftenkf_batch_schedule")
+    return list(bt), list(sc)
+
+
+def fftenkf_batch_last_device_status(b, stream=None) -> int:
+    return lib().fftenkf_batch_last_device_status(b, stream)

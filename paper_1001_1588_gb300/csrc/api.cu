@@ -41,6 +41,10 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 }  // namespace
 
+namespace fftenkf {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace fftenkf
+
 struct fftenkf_plan_s {
   int ny, nx, L, M, N, storage;
   int n_obs, n_un;
