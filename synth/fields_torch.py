@@ -92,3 +92,32 @@ def make_config3_torch(device="cuda", seed: int = 20260003, ny: int = 4096, nx: 
     return DeviceProblem(ny=ny, nx=nx, M=M, N=N, observed=list(observed), obs=obs, n_obs=n_obs,
                          ensemble=ens, data=data, perturbations=pert, rhat=rhat, truth=truth,
                          storage=storage, seed=seed)
+
+
+def se_half(ny: int, nx: int, ell: float, device) -> torch.Tensor:
+    S = torch.exp(-2.0 * math.pi ** 2 * ell ** 2 * _xi2_half(ny, nx, device))
+    return _normalise_half(S, nx, 1.0)
+
+
+def make_batched_torch(device="cuda", count: int = 256, seed: int = 20260004, storage=torch.float32,
+                       sides=None, n_range=(5, 25)):
+    """The batched workload (independent single-block analyses of uneven sizes) drawn on the
+    device: shapes and parameters from synth.fields.batched_item_params, SE fields, flat rhat."""
+    from .fields import BATCH_SIDES, batched_item_params
+    items = []
+    for it in batched_item_params(count, seed, sides or BATCH_SIDES, n_range):
+        ny, nx, N = it["ny"], it["nx"], it["N"]
+        g = torch.Generator(device=device)
+        g.manual_seed(it["seed"])
+        sq = se_half(ny, nx, it["ell"], device).sqrt().to(torch.float32)
+        truth = _field(sq, torch.randn(ny, nx, device=device, generator=g), ny, nx)
+        ens = torch.empty(N, ny, nx, device=device, dtype=storage)
+        for k in range(N):
+            ens[k] = _field(sq, torch.randn(ny, nx, device=device, generator=g), ny, nx).to(storage)
+        r = it["r"]
+        data = (truth + math.sqrt(r) * torch.randn(ny, nx, device=device, generator=g)).contiguous()
+        pert = (math.sqrt(r) * torch.randn(N, ny, nx, device=device, generator=g)).to(storage).contiguous()
+        rhat = torch.full((ny, nx // 2 + 1), r, device=device, dtype=torch.float64)
+        items.append(DeviceProblem(ny=ny, nx=nx, N=N, ensemble=ens, data=data, perturbations=pert, rhat=rhat,
+                                   truth=truth, ell=it["ell"], r=r))
+    return items

@@ -66,7 +66,7 @@ def test_batched_mixed_sizes(abi):
 
 
 def test_batched_autotune_and_edge_sizes(abi):
-    specs = [(16, 16, 2), (24, 48, 3), (1024, 1024, 3), (512, 2048, 2), (48, 32, 25), (768, 768, 4)]
+    specs = [(16, 32, 2), (24, 48, 3), (1024, 1024, 3), (512, 2048, 2), (48, 32, 25), (768, 768, 4)]
     items = []
     for i, (ny, nx, N) in enumerate(specs):
         S = fields.se_spectrum(ny, nx, 2.0 + i, 1.0)
