@@ -165,6 +165,39 @@ fftenkf_status fftenkf_batch_autotune(fftenkf_batch batch, void* workspace, void
 fftenkf_status fftenkf_batch_schedule(fftenkf_batch batch, int* cta_threads, int* sched, int n);
 fftenkf_status fftenkf_batch_last_device_status(fftenkf_batch batch, void* stream);
 
+/* ---------------------------------------------------------------- learned spectrum
+ * A spectral-variance denoiser (not part of the paper's method, which only
+ * motivates estimating the covariance from a very small ensemble, Sec. 2.1):
+ * the single-table chat of eq. (dii) is reduced to 128 radial bins of log chat
+ * (|k| = sqrt(k_y^2 + k_x^2), bin width sqrt(ny^2+nx^2)/256, bin decisions in
+ * FP64), a 256 -> 64 -> 64 -> 64 -> 128 GELU MLP (BF16 weights, FP32
+ * accumulation) maps the bin values minus their mean plus log bin centres to
+ * the binned log spectrum of a large ensemble, and the result is interpolated
+ * back to every wavenumber.  Parameters: one flat float vector of
+ * fftenkf_mlp_param_count() values [W1 (64x256, row = output), b1, W2 (64x64),
+ * b2, W3, b3, W4 (128x64), b4]; forward and backward use their BF16 rounding.
+ * All array arguments are device pointers; spectra are [ny][nx/2+1] double. */
+typedef struct fftenkf_denoiser_s* fftenkf_denoiser;
+int fftenkf_mlp_param_count(void);
+fftenkf_status fftenkf_denoiser_create(fftenkf_denoiser* d, int ny, int nx, int trained_members);
+fftenkf_status fftenkf_denoiser_destroy(fftenkf_denoiser d);
+/* features [batch][256] float and removed means [batch] of `batch` consecutive chat tables */
+fftenkf_status fftenkf_denoiser_features(fftenkf_denoiser d, const double* chat, int batch, float* features,
+                                         float* means, void* stream);
+/* network outputs [batch][128] (binned log spectrum minus the input mean) */
+fftenkf_status fftenkf_mlp_forward(const float* params, const float* features, int batch, float* out, void* stream);
+/* gradient of mean((out - targets)^2) over batch x 128 into grads (overwritten), loss into *loss (device) */
+fftenkf_status fftenkf_mlp_gradient(const float* params, const float* features, const float* targets, int batch,
+                                    float* grads, float* loss, void* stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step counts from 1) */
+fftenkf_status fftenkf_mlp_adam(float* params, float* m, float* v, const float* grads, int step, float lr,
+                                void* stream);
+/* chat_out = learned spectrum of chat_in; the plain chat_in is copied instead when n_members differs
+ * from the trained ensemble size or the network output is not finite.  used_fallback (HOST, may be
+ * NULL; non-NULL makes the call wait for the stream) receives 1 when the plain estimate was used. */
+fftenkf_status fftenkf_denoise_spectrum(fftenkf_denoiser d, const float* params, const double* chat_in,
+                                        double* chat_out, int n_members, int* used_fallback, void* stream);
+
 /* Static description of a status code. */
 const char* fftenkf_status_string(fftenkf_status s);
 /* Message of the last failing call on this host thread ("" if none). */

@@ -61,6 +61,18 @@ _SIGNATURES = [
     ("fftenkf_batch_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_batch_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fftenkf_mlp_param_count", ctypes.c_int, []),
+    ("fftenkf_denoiser_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("fftenkf_denoiser_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("fftenkf_denoiser_features", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    ("fftenkf_mlp_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fftenkf_mlp_gradient", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fftenkf_mlp_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_float, ctypes.c_void_p]),
+    ("fftenkf_denoise_spectrum", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     ("fftenkf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_last_error", ctypes.c_char_p, []),
 ]
@@ -222,3 +234,44 @@ def fftenkf_batch_schedule(b, n=7):
 
 def fftenkf_batch_last_device_status(b, stream=None) -> int:
     return lib().fftenkf_batch_last_device_status(b, stream)
+
+
+# ---------------------------------------------------------------- learned spectrum
+def fftenkf_mlp_param_count() -> int:
+    return lib().fftenkf_mlp_param_count()
+
+
+def fftenkf_denoiser_create(ny, nx, trained_members=5):
+    d = ctypes.c_void_p()
+    check(lib().fftenkf_denoiser_create(ctypes.byref(d), ny, nx, trained_members), "fftenkf_denoiser_create")
+    return d.value
+
+
+def fftenkf_denoiser_destroy(d):
+    check(lib().fftenkf_denoiser_destroy(d), "fftenkf_denoiser_destroy")
+
+
+def fftenkf_denoiser_features(d, chat, batch, features, means, stream=None):
+    check(lib().fftenkf_denoiser_features(d, _p(chat), batch, _p(features), _p(means), stream),
+          "fftenkf_denoiser_features")
+
+
+def fftenkf_mlp_forward(params, features, batch, out, stream=None):
+    check(lib().fftenkf_mlp_forward(_p(params), _p(features), batch, _p(out), stream), "fftenkf_mlp_forward")
+
+
+def fftenkf_mlp_gradient(params, features, targets, batch, grads, loss, stream=None):
+    check(lib().fftenkf_mlp_gradient(_p(params), _p(features), _p(targets), batch, _p(grads), _p(loss), stream),
+          "fftenkf_mlp_gradient")
+
+
+def fftenkf_mlp_adam(params, m, v, grads, step, lr, stream=None):
+    check(lib().fftenkf_mlp_adam(_p(params), _p(m), _p(v), _p(grads), step, lr, stream), "fftenkf_mlp_adam")
+
+
+def fftenkf_denoise_spectrum(d, params, chat_in, chat_out, n_members, stream=None, want_flag=True):
+    flag = ctypes.c_int(0)
+    check(lib().fftenkf_denoise_spectrum(d, _p(params), _p(chat_in), _p(chat_out), n_members,
+                                         ctypes.byref(flag) if want_flag else None, stream),
+          "fftenkf_denoise_spectrum")
+    return flag.value
