@@ -48,7 +48,8 @@ def unpack(theta):
 
 
 def radial(ny: int, nx: int):
-    ky = np.fft.fftfreq(ny) * ny
+    j = np.arange(ny)
+    ky = np.where(j <= ny // 2, j, j - ny).astype(np.float64)   # exact integer wavenumbers
     kx = np.arange(nx // 2 + 1, dtype=np.float64)
     kabs = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
     w = sqrt(ny * ny + nx * nx) / 2.0 / N_BINS

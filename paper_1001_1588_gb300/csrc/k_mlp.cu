@@ -22,22 +22,23 @@ constexpr int SB = 8;                        // samples per CTA
 // ----------------------------------------------------------------- binning
 // chat: [B][ny][L+1] f64 (one real table per sample); bins: [ny][L+1] uint8 bin
 // index (FP64 decision, made on the host); feat: [B][256] f32; mean: [B] f32
-__global__ void __launch_bounds__(256) mlp_bin_kernel(const double* __restrict__ chat, const uint8_t* __restrict__ bins,
+// bin_order: the K1 half-spectrum entries grouped by bin (ascending), bin_start[129]
+// their offsets: every warp reduces whole bins (lane partial sums, then a tree
+// over the lanes), so no floating-point atomics and a short summation chain.
+__global__ void __launch_bounds__(256) mlp_bin_kernel(const double* __restrict__ chat,
+                                                      const uint32_t* __restrict__ bin_order,
+                                                      const uint32_t* __restrict__ bin_start,
                                                       const float* __restrict__ centre_log, int K1,
                                                       float* __restrict__ feat, float* __restrict__ mean) {
-  // one conversion to float per entry; log(max(c, 1e-30 cmax)) evaluated as
-  // log(max(c/cmax, 1e-30)) + log(cmax) so that the floor never underflows
-  __shared__ float sums[kBins];
-  __shared__ int cnt[kBins];
+  // log(max(c, 1e-30 cmax)) is evaluated as log(max(c/cmax, 1e-30)) + log(cmax)
+  // so that the floor never underflows; one conversion to float per entry
+  __shared__ float vals[kBins];
   __shared__ float red[256];
+  __shared__ float mu_s;
   const double* c = chat + (size_t)blockIdx.x * K1;
   float mx = 0.f;
   for (int i = threadIdx.x; i < K1; i += blockDim.x) mx = fmaxf(mx, (float)c[i]);
   red[threadIdx.x] = mx;
-  if (threadIdx.x < kBins) {
-    sums[threadIdx.x] = 0.f;
-    cnt[threadIdx.x] = 0;
-  }
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
@@ -45,21 +46,18 @@ __global__ void __launch_bounds__(256) mlp_bin_kernel(const double* __restrict__
   }
   const float cmax = red[0] > 0.f ? red[0] : 1.f;
   const float inv = 1.f / cmax, lmax = logf(cmax);
-  for (int i = threadIdx.x; i < K1; i += blockDim.x) {
-    const float lv = logf(fmaxf((float)c[i] * inv, 1e-30f)) + lmax;
-    atomicAdd(&sums[bins[i]], lv);
-    atomicAdd(&cnt[bins[i]], 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int b = warp; b < kBins; b += nw) {
+    const uint32_t i0 = bin_start[b], i1 = bin_start[b + 1];
+    float acc = 0.f;
+    for (uint32_t i = i0 + lane; i < i1; i += 32) acc += logf(fmaxf((float)c[bin_order[i]] * inv, 1e-30f));
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) vals[b] = (i1 > i0) ? acc / (float)(i1 - i0) + lmax : 0.f;
   }
   __syncthreads();
-  if (threadIdx.x < kBins) {
-    const float v = cnt[threadIdx.x] ? sums[threadIdx.x] / (float)cnt[threadIdx.x] : 0.f;
-    sums[threadIdx.x] = v;
-  }
-  __syncthreads();
-  __shared__ float mu_s;
   if (threadIdx.x < 32) {
     float acc = 0.f;
-    for (int b = threadIdx.x; b < kBins; b += 32) acc += sums[b];
+    for (int b = threadIdx.x; b < kBins; b += 32) acc += vals[b];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (threadIdx.x == 0) mu_s = acc / kBins;
   }
@@ -67,7 +65,7 @@ __global__ void __launch_bounds__(256) mlp_bin_kernel(const double* __restrict__
   const float mu = mu_s;
   float* f = feat + (size_t)blockIdx.x * kIn;
   if (threadIdx.x < kBins) {
-    f[threadIdx.x] = sums[threadIdx.x] - mu;
+    f[threadIdx.x] = vals[threadIdx.x] - mu;
     f[kBins + threadIdx.x] = centre_log[threadIdx.x];
   }
   if (threadIdx.x == 0) mean[blockIdx.x] = mu;
@@ -302,9 +300,9 @@ __global__ void mlp_adam_kernel(float* __restrict__ params, float* __restrict__ 
 int mlp_param_count() { return kParams; }
 int mlp_acts_per_sample() { return kActs; }
 
-cudaError_t launch_mlp_bin(const double* chat, const uint8_t* bins, const float* centre_log, int B, int K1, float* feat,
-                           float* mean, cudaStream_t s) {
-  mlp_bin_kernel<<<B, 256, 0, s>>>(chat, bins, centre_log, K1, feat, mean);
+cudaError_t launch_mlp_bin(const double* chat, const uint32_t* order, const uint32_t* start, const float* centre_log,
+                           int B, int K1, float* feat, float* mean, cudaStream_t s) {
+  mlp_bin_kernel<<<B, 256, 0, s>>>(chat, order, start, centre_log, K1, feat, mean);
   return cudaGetLastError();
 }
 

@@ -9,8 +9,8 @@
 namespace fftenkf {
 void set_last_error(const std::string& msg);
 int mlp_param_count();
-cudaError_t launch_mlp_bin(const double* chat, const uint8_t* bins, const float* centre_log, int B, int K1, float* feat,
-                           float* mean, cudaStream_t s);
+cudaError_t launch_mlp_bin(const double* chat, const uint32_t* order, const uint32_t* start, const float* centre_log,
+                           int B, int K1, float* feat, float* mean, cudaStream_t s);
 cudaError_t launch_mlp_finish(const float* out, const float* mean, float* out_log, int* flag, const double* chat_in,
                               double* chat_out, int K1, int ny, int L, float w, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float* params, const float* X, int B, float* out, float* acts, cudaStream_t s);
@@ -35,7 +35,8 @@ constexpr int kNB = 128;
 struct fftenkf_denoiser_s {
   int ny, nx, L, K1, trained_members;
   float w;                 // bin width in |k| units
-  uint8_t* d_bins = nullptr;
+  uint32_t* d_order = nullptr;   // entries grouped by radial bin
+  uint32_t* d_start = nullptr;   // [129] offsets of the bins in d_order
   float* d_centre_log = nullptr;
   float* d_scratch = nullptr;   // features 256 | mean 1 | out 128 | out_log 128
   int* d_flag = nullptr;
@@ -56,22 +57,30 @@ extern "C" fftenkf_status fftenkf_denoiser_create(fftenkf_denoiser* out, int ny,
   // radial bins decided in FP64: b = min(127, floor(|k| / w)), w = sqrt(ny^2 + nx^2) / 2 / 128
   const double w = std::sqrt((double)ny * ny + (double)nx * nx) / 2.0 / kNB;
   d->w = (float)w;
-  std::vector<uint8_t> bins(d->K1);
+  std::vector<int> bins(d->K1);
+  std::vector<uint32_t> start(kNB + 1, 0);
   for (int ky = 0; ky < ny; ++ky) {
     const double kyv = (ky <= ny / 2) ? ky : ky - ny;
     for (int kx = 0; kx <= d->L; ++kx) {
       const double kabs = std::sqrt(kyv * kyv + (double)kx * kx);
       const double b = std::floor(kabs / w);
-      bins[ky * (d->L + 1) + kx] = (uint8_t)(b > kNB - 1 ? kNB - 1 : b);
+      const int bi = (int)(b > kNB - 1 ? kNB - 1 : b);
+      bins[ky * (d->L + 1) + kx] = bi;
+      start[bi + 1] += 1;
     }
   }
+  for (int b = 0; b < kNB; ++b) start[b + 1] += start[b];
+  std::vector<uint32_t> order(d->K1), fill(start.begin(), start.end() - 1);
+  for (int i = 0; i < d->K1; ++i) order[fill[bins[i]]++] = (uint32_t)i;
   std::vector<float> cl(kNB);
   for (int b = 0; b < kNB; ++b) {
     const double c = (b + 0.5) * w;
     cl[b] = (float)std::log(c > 0.5 ? c : 0.5);
   }
-  cudaError_t e = cudaMalloc(&d->d_bins, d->K1);
-  if (e == cudaSuccess) e = cudaMemcpy(d->d_bins, bins.data(), d->K1, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(&d->d_order, d->K1 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_order, order.data(), d->K1 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_start, (kNB + 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_start, start.data(), (kNB + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&d->d_centre_log, kNB * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(d->d_centre_log, cl.data(), kNB * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&d->d_scratch, (256 + 4 + 2 * kNB) * sizeof(float));
@@ -86,7 +95,8 @@ extern "C" fftenkf_status fftenkf_denoiser_create(fftenkf_denoiser* out, int ny,
 
 extern "C" fftenkf_status fftenkf_denoiser_destroy(fftenkf_denoiser d) {
   if (!d) return FFTENKF_OK;
-  if (d->d_bins) cudaFree(d->d_bins);
+  if (d->d_order) cudaFree(d->d_order);
+  if (d->d_start) cudaFree(d->d_start);
   if (d->d_centre_log) cudaFree(d->d_centre_log);
   if (d->d_scratch) cudaFree(d->d_scratch);
   if (d->d_flag) cudaFree(d->d_flag);
@@ -98,7 +108,7 @@ extern "C" fftenkf_status fftenkf_denoiser_features(fftenkf_denoiser d, const do
                                                     float* means, void* stream) {
   set_last_error("");
   if (!d || !chat || !features || !means || batch <= 0) return mfail(FFTENKF_EINVAL, "bad arguments");
-  return mcuda(launch_mlp_bin(chat, d->d_bins, d->d_centre_log, batch, d->K1, features, means,
+  return mcuda(launch_mlp_bin(chat, d->d_order, d->d_start, d->d_centre_log, batch, d->K1, features, means,
                               static_cast<cudaStream_t>(stream)),
                "denoiser_features");
 }
@@ -140,7 +150,7 @@ extern "C" fftenkf_status fftenkf_denoise_spectrum(fftenkf_denoiser d, const flo
   float* mean = feat + 256;
   float* out = mean + 4;
   float* out_log = out + kNB;
-  cudaError_t e = launch_mlp_bin(chat_in, d->d_bins, d->d_centre_log, 1, d->K1, feat, mean, s);
+  cudaError_t e = launch_mlp_bin(chat_in, d->d_order, d->d_start, d->d_centre_log, 1, d->K1, feat, mean, s);
   if (e == cudaSuccess) e = launch_mlp_forward(params, feat, 1, out, nullptr, s);
   if (e == cudaSuccess)
     e = launch_mlp_finish(out, mean, out_log, d->d_flag, chat_in, chat_out, d->K1, d->ny, d->L, d->w, s);

@@ -29,7 +29,14 @@ def _rel(a, b):
 
 
 def _bf16(theta):
-    return torch.from_numpy(np.asarray(theta, np.float32)).to(torch.bfloat16).double().numpy()
+    """The network the kernels evaluate: weights rounded to BF16, biases kept in FP32."""
+    t = np.asarray(theta, np.float32).astype(np.float64).copy()
+    pos = 0
+    for i, o in mlp.LAYERS:
+        w = t[pos:pos + i * o]
+        t[pos:pos + i * o] = torch.from_numpy(w.astype(np.float32)).to(torch.bfloat16).double().numpy()
+        pos += i * o + o
+    return t
 
 
 def _theta(seed=1):

@@ -65,3 +65,10 @@ def test_adam_first_step_is_sign_times_lr():
     g = np.array([0.5, -2.0, 1e-3])
     th, m, v = mlp.adam(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
     np.testing.assert_allclose(th, -0.01 * np.sign(g), rtol=1e-5)
+
+
+def test_bin_decisions_use_exact_integer_wavenumbers():
+    """|k| on bin boundaries (|k|/w integer) must fall in the upper bin: 96 x 128 has w = 0.625."""
+    kabs, b, centres = mlp.radial(96, 128)
+    assert kabs[25, 0] == 25.0 and b[25, 0] == 40
+    assert kabs[96 - 15, 20] == 25.0 and b[96 - 15, 20] == 40
