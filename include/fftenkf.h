@@ -110,6 +110,29 @@ fftenkf_status fftenkf_analyze(fftenkf_plan plan, void* ensemble, const float* d
                                const void* perturbations, const double* rhat, const double* spectrum,
                                void* workspace, void* stream);
 
+/* Allocation-free estimate for one block (the paper has no counterpart: this
+ * is a deployment variant of fftenkf_estimate_spectrum).  For callers that may
+ * not call cudaMalloc -- e.g. a host framework that owns every device
+ * allocation through its own pool, or a latency-critical loop that cannot
+ * afford cudaMalloc's implicit synchronisation -- it needs no plan and no
+ * workspace: all scratch (twiddle tables, mean, row spectra, covariance table,
+ * status word) comes from one static device array of 64 MiB that every GPU
+ * loading this library holds until the process exits.  It allocates nothing
+ * and calls no allocating routine.
+ *   ensemble      [N][ny][nx] device array of the storage type (one block)
+ *   spectrum_out  [ny][nx/2+1] device doubles: chat of eq. (dii), unitary scaling
+ * Sizes follow the plan limits; a problem whose scratch exceeds the array
+ * (about N (nx/2) ny 8 + ny nx 4 bytes plus small tables > 64 MiB) returns
+ * FFTENKF_EUNSUPPORTED with a message giving the bytes needed.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it, so make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * contents; calls that overlap on the GPU (on different streams, or from
+ * different host threads) race on it and must be serialised by the caller.
+ * Non-finite covariance values appear in spectrum_out as such. */
+fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble, int ny, int nx, int n_members, int storage,
+                                                double* spectrum_out, void* stream);
+
 /* Wait for `stream`, then return and clear the plan's device status word:
  * FFTENKF_OK, FFTENKF_ENONFINITE, or FFTENKF_ECUDA if the stream reported an
  * error. */

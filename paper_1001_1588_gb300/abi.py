@@ -44,6 +44,8 @@ _SIGNATURES = [
     ("fftenkf_spectrum_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("fftenkf_estimate_spectrum", ctypes.c_int, [ctypes.c_void_p] * 5),
     ("fftenkf_analyze", ctypes.c_int, [ctypes.c_void_p] * 8),
+    ("fftenkf_estimate_spectrum_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("fftenkf_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("fftenkf_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("fftenkf_pass_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -152,6 +154,12 @@ def fftenkf_estimate_spectrum(plan, ensemble, spectrum_out, workspace=None, stre
 def fftenkf_analyze(plan, ensemble, data, perturbations, rhat, spectrum=None, workspace=None, stream=None):
     check(lib().fftenkf_analyze(plan, _p(ensemble), _p(data), _p(perturbations), _p(rhat), _p(spectrum),
                                 _p(workspace), stream), "fftenkf_analyze")
+
+
+def fftenkf_estimate_spectrum_static(ensemble, ny, nx, n_members, storage, spectrum_out, stream=None):
+    """Allocation-free single-block estimate (scratch in the library's static device array)."""
+    check(lib().fftenkf_estimate_spectrum_static(_p(ensemble), ny, nx, n_members, storage, _p(spectrum_out), stream),
+          "fftenkf_estimate_spectrum_static")
 
 
 def fftenkf_last_device_status(plan, stream=None) -> int:
