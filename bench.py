@@ -83,8 +83,9 @@ def pass_bytes(ny, nx, M, N, n_obs, s):
     return {
         "mean": M * N * G * s + M * G * 4,
         "row_fwd_anomaly": M * N * G * s + M * G * 4 + M * N * line,
-        "col_stats": M * N * line + nf * K1 * 4,
-        "gain": nf * K1 * 4 + n_obs * K1 * 8 + nf * K1 * 4,
+        "rhat_transpose": 2 * n_obs * K1 * 8,
+        "col_stats": M * N * line + n_obs * K1 * 8 + nf * K1 * 4,      # rows in, rhat in, gains out
+        "gain": nf * K1 * 4 + n_obs * K1 * 8 + nf * K1 * 4,            # caller-spectrum analyses only
         "row_fwd_innovation": 2 * n_obs * N * G * s + n_obs * G * 4 + n_obs * N * line,
         "col_update": n_obs * N * line + nf * K1 * 4 + M * N * line,
         "row_inv": M * N * line + 2 * M * N * G * s,

@@ -1,14 +1,16 @@
 // C ABI: plans, argument validation and the order of the passes.
 //
 // analyze (Sec. 2.1, eq. spectral-multi-enkf), on the caller's stream unless noted:
+//   0. rhat_transpose  rhat to the column layout            [auxiliary stream, overlaps 1-2]
 //   1. mean            ubar^(j) over members                          (eq. dii)
 //   2. row_fwd anomaly  rows of F(u_k^(j) - ubar^(j)) -> A
-//   3. col_stats       columns of F, chat^(oo), chat^(jo) -> chat_t   (eq. dii, cov-multi-spectral)
-//   4. gain            FP64 gains -> goo, gjo          [auxiliary stream, overlaps 5]
+//   3. col_stats       columns of F, chat^(oo), chat^(jo) and the gains
+//                      chat/(chat^(oo)+rhat) -> goo, gjo (eq. dii, cov-multi-spectral, spectral-multi-enkf)
 //   5. row_fwd innov   rows of F(d_o + e_{k,o} - u_k^(o)) -> W
 //   6. col_update      gain x innovation, inverse columns -> S (aliases A)
 //   7. row_inv         inverse rows, u_k^(j) += increment
-// With a caller-supplied spectrum, 1-3 are skipped and 4 reads the tables.
+// With a caller-supplied spectrum, 1-3 are skipped and the gain pass (4) reads the
+// tables on the auxiliary stream, overlapping 5.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -22,9 +24,10 @@
 using namespace fftenkf;
 
 enum Pass { kPassMean, kPassRowAnom, kPassStats, kPassGain, kPassRowInnov, kPassUpdate, kPassRowInv,
-            kPassChatOut, kPassCount };
+            kPassChatOut, kPassRhatT, kPassCount };
 static const char* kPassNames[kPassCount] = {"mean", "row_fwd_anomaly", "col_stats", "gain",
-                                             "row_fwd_innovation", "col_update", "row_inv", "chat_out"};
+                                             "row_fwd_innovation", "col_update", "row_inv", "chat_out",
+                                             "rhat_transpose"};
 
 namespace {
 thread_local std::string g_last_error;
@@ -57,7 +60,7 @@ struct fftenkf_plan_s {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // workspace layout (byte offsets)
-  size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, ws_bytes;
+  size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, off_rhat_t, ws_bytes;
   void* own_ws = nullptr;
   int device = 0;
   // per-pass CUDA-event timing (fftenkf_set_profiling); a ring of event pairs per pass
@@ -175,6 +178,7 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
   p->off_W = off;    off = round_up(off + (size_t)p->N * p->n_obs * line, 256);
   p->off_goo = off;  off = round_up(off + (size_t)p->n_obs * tab * sizeof(float), 256);
   p->off_gjo = off;  off = round_up(off + (size_t)p->n_obs * p->n_un * tab * sizeof(float2), 256);
+  p->off_rhat_t = off; off = round_up(off + (size_t)p->n_obs * tab * sizeof(double), 256);
   p->ws_bytes = off;
   cudaGetDevice(&p->device);
   std::vector<float2> tw;
@@ -253,7 +257,9 @@ static fftenkf_status get_workspace(fftenkf_plan p, void* ws, char** out) {
 }
 
 // steps 1-3: mean, anomaly row spectra, column statistics -> chat_t
-static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s) {
+// with rhat_t != null the column pass also forms the gains (analysis) and skips chat_t
+static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s, const double* rhat_t,
+                                  cudaEvent_t wait_before_stats = nullptr) {
   MeanParams mp;
   mp.M = p->M;
   mp.N = p->N;
@@ -283,11 +289,19 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   for (int i = 0; i < p->n_obs; ++i) cp.obs[i] = p->obs[i];
   for (int u = 0; u < p->n_un; ++u) cp.un[u] = p->un[u];
   cp.A = rp.out;
-  cp.chat = reinterpret_cast<float*>(ws + p->off_chat);
+  cp.chat = rhat_t ? nullptr : reinterpret_cast<float*>(ws + p->off_chat);
+  cp.rhat_t = rhat_t;
+  cp.goo = reinterpret_cast<float*>(ws + p->off_goo);
+  cp.gjo = reinterpret_cast<float2*>(ws + p->off_gjo);
+  cp.inv_G = (float)(1.0 / ((double)p->ny * (double)p->nx));
   cp.scale = (float)(1.0 / ((double)(p->N - 1) * (double)p->ny * (double)p->nx));
   cp.vsel = p->sched[kPassStats];
   cp.twY = p->twY(cp.vsel);
   cp.status = p->d_status;
+  if (wait_before_stats) {
+    e = cudaStreamWaitEvent(s, wait_before_stats, 0);
+    if (e != cudaSuccess) return e;
+  }
   prof_begin(p, kPassStats, s);
   e = launch_col_stats(cp, s);
   prof_end(p, kPassStats, s);
@@ -304,7 +318,7 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum(fftenkf_plan p, const void* 
   fftenkf_status st = get_workspace(p, workspace, &ws);
   if (st != FFTENKF_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = run_statistics(p, ensemble, ws, s);
+  cudaError_t e = run_statistics(p, ensemble, ws, s, nullptr);
   prof_begin(p, kPassChatOut, s);
   if (e == cudaSuccess)
     e = launch_chat_out(reinterpret_cast<float*>(ws + p->off_chat), spectrum_out, p->ny, p->L, p->n_obs, p->n_un, s);
@@ -327,24 +341,36 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   if (st != FFTENKF_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
-  if (!spectrum) e = run_statistics(p, ensemble, ws, s);
-  // gains on the auxiliary stream, overlapping the innovation row pass
-  if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+  // auxiliary stream: rhat transposed for the gains (estimated spectrum) or the gain pass
+  // (caller spectrum), overlapping the passes on the caller's stream
+  e = cudaEventRecord(p->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
   GainParams gp;
   memset(&gp, 0, sizeof(gp));
   gp.ny = p->ny; gp.L = p->L; gp.n_obs = p->n_obs; gp.n_un = p->n_un;
-  gp.chat_t = spectrum ? nullptr : reinterpret_cast<const float*>(ws + p->off_chat);
   gp.spec = spectrum;
   gp.rhat = rhat;
   gp.goo = reinterpret_cast<float*>(ws + p->off_goo);
   gp.gjo = reinterpret_cast<float2*>(ws + p->off_gjo);
   gp.scale = (float)(1.0 / ((double)p->ny * (double)p->nx));
   gp.status = p->d_status;
-  prof_begin(p, kPassGain, p->aux);
-  if (e == cudaSuccess) e = launch_gain(gp, p->aux);
-  prof_end(p, kPassGain, p->aux);
+  double* rhat_t = reinterpret_cast<double*>(ws + p->off_rhat_t);
+  if (!spectrum) {
+    prof_begin(p, kPassRhatT, p->aux);
+    if (e == cudaSuccess) e = launch_rhat_transpose(rhat, rhat_t, p->n_obs, p->ny, p->L, p->aux);
+    prof_end(p, kPassRhatT, p->aux);
+  } else {
+    prof_begin(p, kPassGain, p->aux);
+    if (e == cudaSuccess) e = launch_gain(gp, p->aux);
+    prof_end(p, kPassGain, p->aux);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
+  if (!spectrum) {
+    // mean and anomaly rows need no rhat; the statistics pass (which forms the gains) waits for it
+    if (e == cudaSuccess) e = run_statistics(p, ensemble, ws, s, rhat_t, p->ev_join);
+  } else {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+  }
   RowFwdParams rp;
   memset(&rp, 0, sizeof(rp));
   rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
@@ -357,7 +383,6 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   prof_begin(p, kPassRowInnov, s);
   if (e == cudaSuccess) e = launch_row_fwd(rp, p->N * p->n_obs, s);
   prof_end(p, kPassRowInnov, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
   ColUpdParams up;
   memset(&up, 0, sizeof(up));
   up.ny = p->ny; up.L = p->L; up.M = p->M; up.N = p->N; up.n_obs = p->n_obs; up.n_un = p->n_un;

@@ -84,8 +84,13 @@ struct ColStatsParams {
   int obs[kMaxObs];
   int un[kMaxBlocks];
   const float2* A;        // anomaly row spectra, field j*N+k
-  float* chat;            // [n_obs][L+1][ny] real, then [n_obs*n_un][L+1][ny] float2
+  float* chat;            // [n_obs][L+1][ny] real, then [n_obs*n_un][L+1][ny] float2 (null: not written)
   float scale;            // 1 / ((N-1) * ny * nx)
+  // gains in the epilogue (analysis): rhat transposed to [n_obs][L+1][ny]; null = no gains
+  const double* rhat_t;
+  float* goo;             // [n_obs][L+1][ny]
+  float2* gjo;            // [n_obs*n_un][L+1][ny]
+  float inv_G;            // 1 / (ny nx)
   const float2* twY;      // stage-major twiddles of the ny-point plan
   int* status;
   int vsel;
@@ -125,6 +130,8 @@ cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s);
 cudaError_t launch_gain(const GainParams& p, cudaStream_t s);
 cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, int n_obs, int n_un,
                             cudaStream_t s);
+// rhat [n][ny][L+1] -> rhat_t [n][L+1][ny]
+cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s);
 bool line_supported(int n);       // column line lengths
 bool row_line_supported(int n);   // row line lengths (nx/2)
 // shared-memory bytes a pass needs (0 = unsupported), for plan-time checks

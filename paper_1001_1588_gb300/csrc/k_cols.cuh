@@ -22,6 +22,17 @@
 
 namespace fftenkf {
 
+// 1/x in FP64 for normal x > 0: the approximate reciprocal refined by two steps of
+// the Newton-Raphson iteration for f(y) = 1/y - x (e <- 1 - x y, y <- y + y e).
+__device__ __forceinline__ double recip64_ex(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 template <int NY, int V>
 __device__ __forceinline__ void read_line(float2 (&v)[V], const float2* __restrict__ src, int t, int part) {
   constexpr int T = NY / V;
@@ -138,24 +149,42 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
     if (active) {
       const size_t tab = (size_t)(p.L + 1) * NY;
       bool bad = false;
+      float2* xout = p.chat ? reinterpret_cast<float2*>(p.chat + p.n_obs * tab) : nullptr;
       for (int i = 0; i < p.n_obs; ++i) {
 #pragma unroll
         for (int m = 0; m < V; ++m) {
           const int ky = t + T * m;
+          const size_t at = (size_t)c * NY + ky;
           const float val = acc[i * NY + ky] * p.scale;
           bad |= !isfinite(val);
-          p.chat[i * tab + (size_t)c * NY + ky] = val;
-        }
-      }
-      float2* xout = reinterpret_cast<float2*>(p.chat + p.n_obs * tab);
-      for (int q = 0; q < p.n_obs * p.n_un; ++q) {
-#pragma unroll
-        for (int m = 0; m < V; ++m) {
-          const int ky = t + T * m;
-          const float2 a = xacc[(size_t)q * NY + ky];
-          const float2 val = make_float2(a.x * p.scale, a.y * p.scale);
-          bad |= !(isfinite(val.x) && isfinite(val.y));
-          xout[q * tab + (size_t)c * NY + ky] = val;
+          if (p.chat) p.chat[i * tab + at] = val;
+          if (p.rhat_t) {
+            // eq. (spectral-multi-enkf): G = chat / (chat^(oo) + rhat).  The sum and its
+            // reciprocal are formed in FP64, where chat << rhat keeps chat's digits.
+            const double den = (double)val + p.rhat_t[i * tab + at];
+            // scaled reciprocal 1/(den ny nx) as float; below 1e-30 (chat and rhat both
+            // vanishing) the products are formed in FP64 so that nothing overflows
+            const bool tiny = !(den > 1e-30);
+            const double rd = (den > 1e-30) ? recip64_ex(den) : ((den > 0.0) ? 1.0 / den : 0.0);
+            const float inv = tiny ? 0.f : (float)(rd * (double)p.inv_G);
+            p.goo[i * tab + at] = tiny ? (float)((double)val * rd * (double)p.inv_G) : val * inv;
+            for (int u = 0; u < p.n_un; ++u) {
+              const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
+              const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
+              bad |= !(isfinite(x.x) && isfinite(x.y));
+              if (xout) xout[(i * p.n_un + u) * tab + at] = x;
+              p.gjo[(i * p.n_un + u) * tab + at] =
+                  tiny ? make_float2((float)((double)x.x * rd * (double)p.inv_G), (float)((double)x.y * rd * (double)p.inv_G))
+                       : make_float2(x.x * inv, x.y * inv);
+            }
+          } else if (xout) {
+            for (int u = 0; u < p.n_un; ++u) {
+              const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
+              const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
+              bad |= !(isfinite(x.x) && isfinite(x.y));
+              xout[(i * p.n_un + u) * tab + at] = x;
+            }
+          }
         }
       }
       if (bad) atomicOr(p.status, kStatusNonFinite);

@@ -149,4 +149,28 @@ cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, int
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) rhat_transpose_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                             int ny, int L1) {
+  __shared__ double tile[TB][TB + 1];
+  const int c0 = blockIdx.x * TB, ky0 = blockIdx.y * TB;
+  const size_t K = (size_t)ny * L1;
+  const double* src = in + blockIdx.z * K;
+  double* dst = out + blockIdx.z * K;
+  for (int yy = threadIdx.y; yy < TB; yy += blockDim.y) {
+    const int ky = ky0 + yy, c = c0 + threadIdx.x;
+    tile[yy][threadIdx.x] = (ky < ny && c < L1) ? src[(size_t)ky * L1 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int cc = threadIdx.y; cc < TB; cc += blockDim.y) {
+    const int c = c0 + cc, ky = ky0 + threadIdx.x;
+    if (c < L1 && ky < ny) dst[(size_t)c * ny + ky] = tile[threadIdx.x][cc];
+  }
+}
+
+cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s) {
+  dim3 grid((L + 1 + TB - 1) / TB, (ny + TB - 1) / TB, n);
+  rhat_transpose_kernel<<<grid, dim3(TB, 8), 0, s>>>(rhat, rhat_t, ny, L + 1);
+  return cudaGetLastError();
+}
+
 }  // namespace fftenkf
