@@ -392,6 +392,8 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   }
   up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
+  up.RS = row_inv_rows(p->L, p->sched[kPassRowInv], p->ny, p->nx, p->storage == FFTENKF_BF16 ? 2 : 4);
+  if (up.RS == 0 && e == cudaSuccess) e = cudaErrorInvalidConfiguration;
   up.vsel = p->sched[kPassUpdate];
   up.twY = p->twY(up.vsel); up.status = p->d_status;
   prof_begin(p, kPassUpdate, s);
@@ -482,7 +484,8 @@ extern "C" fftenkf_status fftenkf_set_schedule(fftenkf_plan p, const int* sched,
     if (next[a] < 0 || next[a] > (row_pass ? 3 : 1)) return fail(FFTENKF_EINVAL, "schedule entry out of range");
   }
   if (p->n_obs > 0 && (col_stats_smem(p->ny, nf, next[kPassStats], nullptr) == 0 ||
-                       col_update_smem(p->ny, p->n_obs, next[kPassUpdate], nullptr, nullptr) == 0))
+                       col_update_smem(p->ny, p->n_obs, next[kPassUpdate], nullptr, nullptr) == 0 ||
+                       row_inv_rows(p->L, next[kPassRowInv], p->ny, p->nx, p->storage == FFTENKF_BF16 ? 2 : 4) == 0))
     return fail(FFTENKF_EUNSUPPORTED, "schedule does not fit in shared memory");
   for (int a = 0; a < kPassCount; ++a) p->sched[a] = next[a];
   return FFTENKF_OK;

@@ -18,6 +18,17 @@
 
 namespace fftenkf {
 
+// (hi + lo) / n for an unevaluated sum hi + lo (an error-free accumulation) and an
+// integer n: q = hi inv_n, corrected by the remainder hi - q n (exact with an FMA,
+// since it is a small multiple of ulp(q)) plus lo.  The result is within one unit of
+// the last place of the exact quotient and equals it whenever that quotient is a
+// float (n equal members give their own value back).  inv_n = 1/n rounded.
+__device__ __forceinline__ float pair_div(float hi, float lo, float n, float inv_n) {
+  const float q = hi * inv_n;
+  const float r = fmaf(-q, n, hi) + lo;
+  return fmaf(r, inv_n, q);
+}
+
 constexpr int kMaxBlocks = 16;
 constexpr int kMaxObs = 4;
 
@@ -71,7 +82,9 @@ struct RowFwdParams {
 
 struct RowInvParams {
   int ny, nx, L, R, M, N, storage, n_tiles;
-  const float2* in;       // row spectra of the increments, field j*N+k
+  // row spectra of the increments, field j*N+k, tiled: [field][ny/R][L][R] (R = rows per
+  // item of the inverse pass, row_inv_rows), so that one item is one contiguous block
+  const float2* in;
   void* ens;              // [M][N][ny][nx], updated in place
   const float2* twL;
   const float2* twX;
@@ -103,7 +116,8 @@ struct ColUpdParams {
   const float2* W;        // innovation row spectra, field k*n_obs+i
   const float* goo;       // [n_obs][L+1][ny]
   const float2* gjo;      // [n_obs*n_un][L+1][ny], table i*n_un+u
-  float2* S;              // increment row spectra, field j*N+k
+  float2* S;              // increment row spectra, field j*N+k, tiled [ny/RS][L][RS]
+  int RS;                 // rows per tile of S (a power of two dividing ny)
   const float2* twY;
   int* status;
   int n_stages;           // innovation prefetch stages (set by the launcher)
@@ -125,6 +139,8 @@ struct GainParams {
 cudaError_t launch_mean(const MeanParams& p, cudaStream_t s);
 cudaError_t launch_row_fwd(const RowFwdParams& p, int n_fields, cudaStream_t s);
 cudaError_t launch_row_inv(const RowInvParams& p, int n_fields, cudaStream_t s);
+// rows per item of the inverse row pass for (nx/2, schedule, ny, nx, storage bytes); 0 = unsupported
+int row_inv_rows(int L, int vsel, int ny, int nx, int es);
 cudaError_t launch_col_stats(const ColStatsParams& p, cudaStream_t s);
 cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s);
 cudaError_t launch_gain(const GainParams& p, cudaStream_t s);

@@ -200,6 +200,24 @@ __host__ __device__ constexpr int twiddle_offset(int N, int V, int s) {
 }
 __host__ __device__ constexpr int twiddle_count(int N, int V) { return twiddle_offset(N, V, num_stages(N, V)); }
 
+// Barrier over the threads that transform one line: the whole CTA (bid 0) or
+// named barrier bid over the line's T threads, when each line owns whole warps
+// and the CTA holds several lines, so that lines progress independently.
+template <int T>
+__device__ __forceinline__ void line_sync(int bid) {
+  if (bid == 0) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bid), "n"(T) : "memory");
+  }
+}
+// barrier id of line group g for line_sync: 1 + g when lines of T threads own whole warps
+// (at most 8 lines per CTA of up to 512 threads), else 0 (the CTA barrier)
+template <int T>
+__device__ __forceinline__ int line_bar(int g) {
+  return (T % 32 == 0 && T >= 64) ? 1 + g : 0;
+}
+
 // ------------------------------------------------------------------ stages
 // Stage S of the Stockham transform; NS = product of the radices before it.
 // Butterfly j reads x[j + r N/R], multiplies by W_N^((j mod NS) r N/(NS R)),
@@ -208,7 +226,7 @@ __host__ __device__ constexpr int twiddle_count(int N, int V) { return twiddle_o
 // canonical slots b + r V/R; the last stage's outputs land in canonical slots.
 template <int N, int V, int S, int NS, bool INV>
 struct Stage {
-  static __device__ __forceinline__ void run(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
+  static __device__ __forceinline__ void run(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw, int bid) {
     constexpr int R = radix_at(N, V, S);
     constexpr int T = N / V;
     constexpr int B = V / R;
@@ -239,24 +257,25 @@ struct Stage {
       }
     }
     if constexpr (!LAST) {
-      __syncthreads();
+      line_sync<T>(bid);
 #pragma unroll
       for (int m = 0; m < V; ++m) v[m] = sm[pidx(t + T * m)];
-      __syncthreads();
-      Stage<N, V, S + 1, NS * R, INV>::run(v, sm, t, tw);
+      line_sync<T>(bid);
+      Stage<N, V, S + 1, NS * R, INV>::run(v, sm, t, tw, bid);
     }
   }
 };
 
 // Unnormalised line DFT, sign -1 (forward) or +1 (INV).  Every thread of the
-// CTA must call it (it contains __syncthreads when the plan has >1 stage).
+// CTA (bid 0) or of the line (bid = line_bar(g)) must call it: it synchronises
+// with line_sync(bid) when the plan has >1 stage.
 // tw: the stage-major twiddle table of (N, V) described above (exp(-2 pi i e/N)
 // values).  sm: this line's padded buffer.
 template <int N, int V, bool INV>
-__device__ __forceinline__ void fft_line(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_line(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw, int bid = 0) {
   static_assert(N % V == 0, "V must divide N");
   static_assert(num_stages(N, V) > 0, "no radix plan");
-  Stage<N, V, 0, 1, INV>::run(v, sm, t, tw);
+  Stage<N, V, 0, 1, INV>::run(v, sm, t, tw, bid);
 }
 
 }  // namespace fftenkf

@@ -42,10 +42,12 @@ __device__ __forceinline__ void batch_mean_unit(const BatchItem& it, int u, int 
       hi[e] = s;
     }
   }
-  const float invN = 1.0f / (float)it.N;
+  const float Nf = (float)it.N, inv_N = 1.0f / Nf;
   float4* dst = reinterpret_cast<float4*>(it.mean + q);
-  dst[0] = make_float4((hi[0] + lo[0]) * invN, (hi[1] + lo[1]) * invN, (hi[2] + lo[2]) * invN, (hi[3] + lo[3]) * invN);
-  dst[1] = make_float4((hi[4] + lo[4]) * invN, (hi[5] + lo[5]) * invN, (hi[6] + lo[6]) * invN, (hi[7] + lo[7]) * invN);
+  dst[0] = make_float4(pair_div(hi[0], lo[0], Nf, inv_N), pair_div(hi[1], lo[1], Nf, inv_N), pair_div(hi[2], lo[2], Nf, inv_N),
+                       pair_div(hi[3], lo[3], Nf, inv_N));
+  dst[1] = make_float4(pair_div(hi[4], lo[4], Nf, inv_N), pair_div(hi[5], lo[5], Nf, inv_N), pair_div(hi[6], lo[6], Nf, inv_N),
+                       pair_div(hi[7], lo[7], Nf, inv_N));
 }
 
 // ----------------------------------------------------------------- row passes

@@ -33,6 +33,27 @@ __device__ __forceinline__ double recip64_ex(double x) {
   return fma(y, e, y);
 }
 
+// Gains of one wavenumber whose denominator chat^(oo) + rhat is below FLT_MIN (both
+// vanish): the quotients in FP64, 0 where the denominator is 0.  Kept out of line so
+// that the common FP32 path carries none of its instructions.  xa: the first cross
+// accumulator of this wavenumber (stride ny between tables).  Returns false if a
+// cross spectrum is not finite.
+static __device__ __noinline__ bool gains_fp64(float* goo, float2* gjo, float2* xout, const float2* xa, size_t xstride,
+                                        int i, int n_un, size_t at, size_t tab, double den, float val, float inv_G,
+                                        float scale) {
+  bool ok = true;
+  const double rd = (den > 0.0) ? (double)inv_G / den : 0.0;
+  goo[i * tab + at] = (float)((double)val * rd);
+  for (int u = 0; u < n_un; ++u) {
+    const float2 a = xa[(size_t)(i * n_un + u) * xstride];
+    const float2 x = make_float2(a.x * scale, a.y * scale);
+    ok &= isfinite(x.x) && isfinite(x.y);
+    if (xout) xout[(i * n_un + u) * tab + at] = x;
+    gjo[(i * n_un + u) * tab + at] = make_float2((float)((double)x.x * rd), (float)((double)x.y * rd));
+  }
+  return ok;
+}
+
 template <int NY, int V>
 __device__ __forceinline__ void read_line(float2 (&v)[V], const float2* __restrict__ src, int t, int part) {
   constexpr int T = NY / V;
@@ -116,7 +137,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
         if (l + 1 < lines_per_col) issue(cb, l + 1);
         else if (cb + col_step < ncol) issue(cb + col_step, 0);
       }
-      fft_line<NY, V, false>(v, line, t, p.twY);
+      fft_line<NY, V, false>(v, line, t, p.twY, line_bar<T>(g));
       if (b < p.n_obs) {
 #pragma unroll
         for (int i = 0; i < NOBS; ++i) {
@@ -150,39 +171,52 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
       const size_t tab = (size_t)(p.L + 1) * NY;
       bool bad = false;
       float2* xout = p.chat ? reinterpret_cast<float2*>(p.chat + p.n_obs * tab) : nullptr;
+      // rhat values are requested E at a time before any of their tables is stored, so the
+      // epilogue waits for one memory latency per E values rather than one per value
+      constexpr int E = (V % 8 == 0) ? 8 : ((V % 4 == 0) ? 4 : V);
+#pragma unroll 1
       for (int i = 0; i < p.n_obs; ++i) {
-#pragma unroll
-        for (int m = 0; m < V; ++m) {
-          const int ky = t + T * m;
-          const size_t at = (size_t)c * NY + ky;
-          const float val = acc[i * NY + ky] * p.scale;
-          bad |= !isfinite(val);
-          if (p.chat) p.chat[i * tab + at] = val;
+#pragma unroll 1
+        for (int m0 = 0; m0 < V; m0 += E) {
+          double rr[E];
           if (p.rhat_t) {
-            // eq. (spectral-multi-enkf): G = chat / (chat^(oo) + rhat).  The sum and its
-            // reciprocal are formed in FP64, where chat << rhat keeps chat's digits.
-            const double den = (double)val + p.rhat_t[i * tab + at];
-            // scaled reciprocal 1/(den ny nx) as float; below 1e-30 (chat and rhat both
-            // vanishing) the products are formed in FP64 so that nothing overflows
-            const bool tiny = !(den > 1e-30);
-            const double rd = (den > 1e-30) ? recip64_ex(den) : ((den > 0.0) ? 1.0 / den : 0.0);
-            const float inv = tiny ? 0.f : (float)(rd * (double)p.inv_G);
-            p.goo[i * tab + at] = tiny ? (float)((double)val * rd * (double)p.inv_G) : val * inv;
-            for (int u = 0; u < p.n_un; ++u) {
-              const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
-              const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
-              bad |= !(isfinite(x.x) && isfinite(x.y));
-              if (xout) xout[(i * p.n_un + u) * tab + at] = x;
-              p.gjo[(i * p.n_un + u) * tab + at] =
-                  tiny ? make_float2((float)((double)x.x * rd * (double)p.inv_G), (float)((double)x.y * rd * (double)p.inv_G))
-                       : make_float2(x.x * inv, x.y * inv);
-            }
-          } else if (xout) {
-            for (int u = 0; u < p.n_un; ++u) {
-              const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
-              const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
-              bad |= !(isfinite(x.x) && isfinite(x.y));
-              xout[(i * p.n_un + u) * tab + at] = x;
+#pragma unroll
+            for (int e = 0; e < E; ++e) rr[e] = __ldg(p.rhat_t + i * tab + (size_t)c * NY + t + T * (m0 + e));
+          }
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int ky = t + T * (m0 + e);
+            const size_t at = (size_t)c * NY + ky;
+            const float val = acc[i * NY + ky] * p.scale;
+            bad |= !isfinite(val);
+            if (p.chat) p.chat[i * tab + at] = val;
+            if (p.rhat_t) {
+              // eq. (spectral-multi-enkf): G = chat / (chat^(oo) + rhat).  The sum is formed in
+              // FP64 (where chat << rhat it keeps chat's digits), then rounded once; the
+              // quotients are FP32; a sum below FLT_MIN takes the FP64 path (gains_fp64).
+              const double den = (double)val + rr[e];
+              const float denf = (float)den;
+              const float inv = __fdividef(p.inv_G, denf);
+              const bool tiny = !(denf >= 1.17549435e-38f);
+              if (tiny) {
+                bad |= !gains_fp64(p.goo, p.gjo, xout, xacc + ky, NY, i, p.n_un, at, tab, den, val, p.inv_G, p.scale);
+              } else {
+                p.goo[i * tab + at] = val * inv;
+                for (int u = 0; u < p.n_un; ++u) {
+                  const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
+                  const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
+                  bad |= !(isfinite(x.x) && isfinite(x.y));
+                  if (xout) xout[(i * p.n_un + u) * tab + at] = x;
+                  p.gjo[(i * p.n_un + u) * tab + at] = make_float2(x.x * inv, x.y * inv);
+                }
+              }
+            } else if (xout) {
+              for (int u = 0; u < p.n_un; ++u) {
+                const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
+                const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
+                bad |= !(isfinite(x.x) && isfinite(x.y));
+                xout[(i * p.n_un + u) * tab + at] = x;
+              }
             }
           }
         }
@@ -295,7 +329,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
     for (int i = 0; i < NOBS; ++i) {
       if (i < p.n_obs) {
         read_line<NY, V>(wv[i], w + (size_t)i * NY, t, part);
-        fft_line<NY, V, false>(wv[i], xbuf, t, p.twY);
+        fft_line<NY, V, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
       } else {
 #pragma unroll
         for (int m = 0; m < V; ++m) wv[i][m] = make_float2(0.f, 0.f);
@@ -341,16 +375,26 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
         if (j + 1 < p.M) issue_g(base, j + 1);
         else if (base + step < n_items) issue_g(base + step, 0);
       }
-      fft_line<NY, V, true>(sv, xbuf, t, p.twY);
+      fft_line<NY, V, true>(sv, xbuf, t, p.twY, line_bar<T>(g));
       if (active) {
-        float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * NY + t;
+        // tiled increment spectra: k_y = RS y_t + r at [y_t][col][r]; RS consecutive k_y of a
+        // warp's stores fill one 8 RS-byte segment
+        float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * p.RS;
+        const size_t tstride = (size_t)p.L * p.RS;
+        const int rs = __ffs(p.RS) - 1;
         if (part == 0) {
 #pragma unroll
-          for (int m = 0; m < V; ++m) dst[T * m] = sv[m];
+          for (int m = 0; m < V; ++m) {
+            const int ky = t + T * m;
+            dst[(size_t)(ky >> rs) * tstride + (ky & (p.RS - 1))] = sv[m];
+          }
         } else {
           float* d1 = reinterpret_cast<float*>(dst) + (part == 1 ? 0 : 1);
 #pragma unroll
-          for (int m = 0; m < V; ++m) d1[2 * T * m] = sv[m].x;
+          for (int m = 0; m < V; ++m) {
+            const int ky = t + T * m;
+            d1[2 * ((size_t)(ky >> rs) * tstride + (ky & (p.RS - 1)))] = sv[m].x;
+          }
         }
       }
     }

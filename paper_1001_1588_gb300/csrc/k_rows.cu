@@ -17,8 +17,9 @@ namespace fftenkf {
 
 // ----------------------------------------------------------------- mean
 // ubar^(j)(x) = (1/N) sum_k u_k^(j)(x).  The sum is carried as an unevaluated
-// pair hi + lo with an error-free two-sum per addition, so the mean is the
-// exact sum divided by N and rounded once to float.
+// pair hi + lo with an error-free two-sum per addition, so it is exact; the mean
+// is its quotient by N to within one unit in the last place (pair_div), exact
+// when that quotient is a float.
 __global__ void __launch_bounds__(256) mean_kernel(const MeanParams p) {
   const long long nvec = p.G / 8;
   const long long total = nvec * p.M;
@@ -29,37 +30,47 @@ __global__ void __launch_bounds__(256) mean_kernel(const MeanParams p) {
     float hi[8], lo[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) hi[e] = lo[e] = 0.f;
-    for (int k = 0; k < p.N; ++k) {
-      const size_t off = ((size_t)j * p.N + k) * (size_t)p.G + (size_t)q * 8;
-      float x[8];
-      if (p.storage == kBF16) {
-        const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(p.ens) + off));
-        const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&raw);
+    // four members' loads in flight before they are summed
+    for (int k0 = 0; k0 < p.N; k0 += 4) {
+      float x[4][8];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          float2 f = __bfloat1622float2(b[e]);
-          x[2 * e] = f.x;
-          x[2 * e + 1] = f.y;
+      for (int kk = 0; kk < 4; ++kk) {
+        const int k = k0 + kk;
+        if (k >= p.N) break;
+        const size_t off = ((size_t)j * p.N + k) * (size_t)p.G + (size_t)q * 8;
+        if (p.storage == kBF16) {
+          const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(p.ens) + off));
+          const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float2 f = __bfloat1622float2(b[e]);
+            x[kk][2 * e] = f.x;
+            x[kk][2 * e + 1] = f.y;
+          }
+        } else {
+          const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(p.ens) + off);
+          float4 a = __ldcs(src), b = __ldcs(src + 1);
+          x[kk][0] = a.x; x[kk][1] = a.y; x[kk][2] = a.z; x[kk][3] = a.w;
+          x[kk][4] = b.x; x[kk][5] = b.y; x[kk][6] = b.z; x[kk][7] = b.w;
         }
-      } else {
-        const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(p.ens) + off);
-        float4 a = __ldcs(src), b = __ldcs(src + 1);
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const float s = hi[e] + x[e];
-        const float bp = s - hi[e];
-        const float err = (hi[e] - (s - bp)) + (x[e] - bp);
-        hi[e] = s;
-        lo[e] += err;
+      for (int kk = 0; kk < 4; ++kk) {
+        if (k0 + kk >= p.N) break;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float s = hi[e] + x[kk][e];
+          const float bp = s - hi[e];
+          const float err = (hi[e] - (s - bp)) + (x[kk][e] - bp);
+          hi[e] = s;
+          lo[e] += err;
+        }
       }
     }
-    const float invN = 1.0f / (float)p.N;
+    const float Nf = (float)p.N, inv_N = 1.0f / Nf;
     float m[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) m[e] = (hi[e] + lo[e]) * invN;
+    for (int e = 0; e < 8; ++e) m[e] = pair_div(hi[e], lo[e], Nf, inv_N);
     float4* dst = reinterpret_cast<float4*>(p.mean + (size_t)j * p.G + (size_t)q * 8);
     dst[0] = make_float4(m[0], m[1], m[2], m[3]);
     dst[1] = make_float4(m[4], m[5], m[6], m[7]);
@@ -171,142 +182,144 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
         else if (q + gridDim.x < Q) issue(q + gridDim.x, 0);
       }
       float2* line = lines + row * pitch;
-      fft_line<L, V, false>(v, line, t, p.twL);
+      fft_line<L, V, false>(v, line, t, p.twL, line_bar<T>(g));
 #pragma unroll
       for (int m = 0; m < V; ++m) line[pidx(t + T * m)] = v[m];
     }
     __syncthreads();
-    // spectrum of the real rows, written transposed: out[c][y0 + r]
+    // spectrum of the real rows, written transposed: out[c][y0 + r].  Columns c and L - c
+    // come from the same pair Z[c], Z[L-c]: with E = (Z[c] + conj Z[L-c]) / 2 and
+    // O = -i (Z[c] - conj Z[L-c]) / 2, X[c] = E + W^c O and X[L-c] = conj(E - W^c O).
     float2* out = p.out + f * (size_t)L * p.ny + y0 + 2 * rp;
     const float2* r0 = lines + (2 * rp) * pitch;
     const float2* r1 = r0 + pitch;
-    for (int c = threadIdx.x / RP; c < L; c += cstep) {
-      float2 res[2];
+    for (int c = threadIdx.x / RP; c <= L / 2; c += cstep) {
       const float2 Z0 = r0[pidx(c)], Z1 = r1[pidx(c)];
-      if (c == 0) {
-        res[0] = make_float2(Z0.x + Z0.y, Z0.x - Z0.y);   // packed: X[0] + i X[L]
-        res[1] = make_float2(Z1.x + Z1.y, Z1.x - Z1.y);
-      } else {
-        const float2 wt = __ldg(p.twX + c);
-        const float2 C0 = r0[pidx(L - c)], C1 = r1[pidx(L - c)];
-        const float2 E0 = make_float2(0.5f * (Z0.x + C0.x), 0.5f * (Z0.y - C0.y));
-        const float2 O0 = make_float2(0.5f * (Z0.y + C0.y), -0.5f * (Z0.x - C0.x));
-        const float2 E1 = make_float2(0.5f * (Z1.x + C1.x), 0.5f * (Z1.y - C1.y));
-        const float2 O1 = make_float2(0.5f * (Z1.y + C1.y), -0.5f * (Z1.x - C1.x));
-        res[0] = cadd(E0, cmul(wt, O0));
-        res[1] = cadd(E1, cmul(wt, O1));
+      if (c == 0) {   // packed: X[0] + i X[L]
+        *reinterpret_cast<float4*>(out) = make_float4(Z0.x + Z0.y, Z0.x - Z0.y, Z1.x + Z1.y, Z1.x - Z1.y);
+        continue;
       }
-      *reinterpret_cast<float4*>(out + (size_t)c * p.ny) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+      const float2 C0 = r0[pidx(L - c)], C1 = r1[pidx(L - c)];
+      float2 wt = __ldg(p.twX + c);
+      wt = make_float2(0.5f * wt.x, 0.5f * wt.y);
+      float2 lo[2], hi[2];
+      const float2 Zs[2] = {Z0, Z1}, Cs[2] = {C0, C1};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 E2 = make_float2(Zs[h].x + Cs[h].x, Zs[h].y - Cs[h].y);   // 2 E
+        const float2 O2 = make_float2(Zs[h].y + Cs[h].y, Cs[h].x - Zs[h].x);   // 2 O
+        const float2 P = cmul(wt, O2);                                          // W^c O
+        lo[h] = make_float2(fmaf(0.5f, E2.x, P.x), fmaf(0.5f, E2.y, P.y));
+        hi[h] = make_float2(fmaf(0.5f, E2.x, -P.x), fmaf(-0.5f, E2.y, P.y));
+      }
+      *reinterpret_cast<float4*>(out + (size_t)c * p.ny) = make_float4(lo[0].x, lo[0].y, lo[1].x, lo[1].y);
+      if (c != L - c)
+        *reinterpret_cast<float4*>(out + (size_t)(L - c) * p.ny) = make_float4(hi[0].x, hi[0].y, hi[1].x, hi[1].y);
     }
     __syncthreads();
   }
 }
 
+// Inverse row pass.  A work item is R rows of one field (R = the rows the CTA
+// transforms at once); its increment spectra are one contiguous tile [L][R] of the
+// tiled layout written by the column update, brought in by one bulk copy while the
+// previous item is transformed, and its forecast rows by one bulk copy into a
+// stage.  The inverse real-FFT twist runs cooperatively over the tile, a pair of
+// columns c, L - c per step, and stages each row in its padded line buffer, which
+// then serves as that row's FFT exchange buffer.
 template <int L, int V>
 __global__ void __launch_bounds__(512, 1) row_inv_kernel(const RowInvParams p) {
   constexpr int T = L / V;
   constexpr int pitch = row_pitch(L);
   extern __shared__ __align__(128) unsigned char smraw[];
-  const int LPC = blockDim.x / T;
-  const int rounds = p.R / LPC;
+  const int R = p.R;                 // a power of two
+  const int rs = __ffs(R) - 1;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
   const int nx = p.nx;
   const size_t G = (size_t)p.ny * nx;
   const int es = (p.storage == kBF16) ? 2 : 4;
-  const uint32_t round_bytes = (uint32_t)LPC * nx * es;
-  float2* lines = reinterpret_cast<float2*>(smraw);
-  unsigned char* stage = smraw + (((size_t)p.R * pitch * sizeof(float2) + 127) & ~(size_t)127);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + round_bytes);
-  int* flag = reinterpret_cast<int*>(bar + 1);
-  const long long Q = (long long)p.M * p.N * p.n_tiles;
+  const uint32_t tile_bytes = (uint32_t)L * R * sizeof(float2);
+  const uint32_t item_bytes = (uint32_t)R * nx * es;
+  float2* tile = reinterpret_cast<float2*>(smraw);
+  float2* lines = reinterpret_cast<float2*>(smraw + ((tile_bytes + 127) & ~127u));
+  unsigned char* stage = reinterpret_cast<unsigned char*>(lines) + (((size_t)R * pitch * sizeof(float2) + 127) & ~(size_t)127);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + item_bytes);   // [0] tile, [1] forecast rows
+  int* flag = reinterpret_cast<int*>(bars + 2);
+  const long long Q = (long long)p.M * p.N * p.n_tiles;   // item q = field q / n_tiles, tile q mod n_tiles
   char* ens = reinterpret_cast<char*>(p.ens);
 
-  auto issue = [&](long long q, int r) {      // forecast rows of the next round
+  auto issue_tile = [&](long long q) {
+    mbar_arrive_expect_tx(&bars[0], tile_bytes);
+    bulk_g2s(tile, p.in + (size_t)q * L * R, tile_bytes, &bars[0]);
+  };
+  auto issue_rows = [&](long long q) {
     const size_t f = q / p.n_tiles;
-    const int tile = (int)(q - (long long)f * p.n_tiles);
-    const size_t row0 = (size_t)tile * p.R + (size_t)r * LPC;
-    mbar_arrive_expect_tx(bar, round_bytes);
-    bulk_g2s(stage, ens + (f * G + row0 * nx) * es, round_bytes, bar);
+    const size_t row0 = (size_t)(q - (long long)f * p.n_tiles) * R;
+    mbar_arrive_expect_tx(&bars[1], item_bytes);
+    bulk_g2s(stage, ens + (f * G + row0 * nx) * es, item_bytes, &bars[1]);
   };
 
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t tph = 0, rph = 0;
   long long q = blockIdx.x;
-  if (threadIdx.x == 0 && q < Q) issue(q, 0);
-  const int RP = p.R >> 1;
-  const int rp = threadIdx.x % RP;
-  const int cstep = blockDim.x / RP;
+  if (threadIdx.x == 0 && q < Q) {
+    issue_tile(q);
+    issue_rows(q);
+  }
   for (; q < Q; q += gridDim.x) {
-    const size_t f = q / p.n_tiles;               // field j*N + k
-    const int tile = (int)(q - (long long)f * p.n_tiles);
-    const int y0 = tile * p.R;
-    {
-      const float2* in = p.in + f * (size_t)L * p.ny + y0 + 2 * rp;
-      float2* s0 = lines + (2 * rp) * pitch;
-      float2* s1 = s0 + pitch;
-      // 8 loads in flight per thread before their values are staged
-      const int c0 = threadIdx.x / RP;
-      const int nper = (L + cstep - 1) / cstep;
-      for (int i0 = 0; i0 < nper; i0 += 8) {
-        float4 v4[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int c = c0 + (i0 + u) * cstep;
-          if (i0 + u < nper && c < L) v4[u] = __ldcs(reinterpret_cast<const float4*>(in + (size_t)c * p.ny));
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int c = c0 + (i0 + u) * cstep;
-          if (i0 + u < nper && c < L) {
-            s0[pidx(c)] = make_float2(v4[u].x, v4[u].y);
-            s1[pidx(c)] = make_float2(v4[u].z, v4[u].w);
-          }
-        }
-      }
+    const size_t f = q / p.n_tiles;
+    const int y0 = (int)(q - (long long)f * p.n_tiles) * R;
+    if (!cta_wait(&bars[0], tph, p.status, flag)) {
+      if (threadIdx.x == 0) mbar_wait_bounded(&bars[1], rph);   // forecast copy may be landing
+      return;
     }
-    __syncthreads();
-    for (int r = 0; r < rounds; ++r) {
-      const int row = r * LPC + g;
-      float2* line = lines + row * pitch;
-      float2 v[V];
-#pragma unroll
-      for (int m = 0; m < V; ++m) {
-        const int c = t + T * m;
-        const float2 X = line[pidx(c)];
-        if (c == 0) {
-          v[m] = make_float2(X.x + X.y, X.x - X.y);
-        } else {
-          const float2 Xc = line[pidx(L - c)];
-          const float2 A = make_float2(X.x + Xc.x, X.y - Xc.y);
-          const float2 B = make_float2(X.x - Xc.x, X.y + Xc.y);
-          const float2 Bw = cmulc(B, __ldg(p.twX + c));
-          v[m] = make_float2(A.x - Bw.y, A.y + Bw.x);
-        }
+    tph ^= 1;
+    // inverse twist: from X[c], X[L-c] of a row, z[c] = A + i B conj(W^c) and
+    // z[L-c] = conj(A - i B conj(W^c)), A = X[c] + conj X[L-c], B = X[c] - conj X[L-c]
+    for (int i = threadIdx.x; i < (L / 2 + 1) * R; i += blockDim.x) {
+      const int c = i >> rs, r = i & (R - 1);
+      float2* line = lines + (size_t)r * pitch;
+      const float2 X = tile[c * R + r];
+      if (c == 0) {   // packed X[0] + i X[L]
+        line[pidx(0)] = make_float2(X.x + X.y, X.x - X.y);
+        continue;
       }
-      __syncthreads();
-      fft_line<L, V, true>(v, line, t, p.twL);
-      if (!cta_wait(bar, phase, p.status, flag)) return;
-      phase ^= 1;
-      const unsigned char* st_row = stage + (size_t)g * nx * es;
-      float2 a[V];
-#pragma unroll
-      for (int m = 0; m < V; ++m) a[m] = load2(st_row, 2 * (size_t)(t + T * m), p.storage);
-      __syncthreads();   // stage consumed
-      if (threadIdx.x == 0) {
-        if (r + 1 < rounds) issue(q, r + 1);
-        else if (q + gridDim.x < Q) issue(q + gridDim.x, 0);
-      }
-      char* urow = ens + (f * G + (size_t)(y0 + row) * nx) * es;
-#pragma unroll
-      for (int m = 0; m < V; ++m)
-        store2(urow, 2 * (size_t)(t + T * m), make_float2(a[m].x + v[m].x, a[m].y + v[m].y), p.storage);
+      const float2 Xm = tile[(L - c) * R + r];
+      const float2 A = make_float2(X.x + Xm.x, X.y - Xm.y);
+      const float2 B = make_float2(X.x - Xm.x, X.y + Xm.y);
+      const float2 Bw = cmulc(B, __ldg(p.twX + c));
+      line[pidx(c)] = make_float2(A.x - Bw.y, A.y + Bw.x);
+      if (c != L - c) line[pidx(L - c)] = make_float2(A.x + Bw.y, Bw.x - A.y);
     }
-    __syncthreads();
+    __syncthreads();   // tile consumed, rows staged
+    if (threadIdx.x == 0 && q + gridDim.x < Q) issue_tile(q + gridDim.x);
+    float2* line = lines + (size_t)g * pitch;
+    float2 v[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = line[pidx(t + T * m)];
+    line_sync<T>(line_bar<T>(g));   // the row is read before the FFT reuses its buffer
+    fft_line<L, V, true>(v, line, t, p.twL, line_bar<T>(g));
+    if (!cta_wait(&bars[1], rph, p.status, flag)) {
+      if (threadIdx.x == 0) mbar_wait_bounded(&bars[0], tph);   // next tile may be landing
+      return;
+    }
+    rph ^= 1;
+    const unsigned char* st_row = stage + (size_t)g * nx * es;
+    float2 a[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) a[m] = load2(st_row, 2 * (size_t)(t + T * m), p.storage);
+    __syncthreads();   // stage consumed
+    if (threadIdx.x == 0 && q + gridDim.x < Q) issue_rows(q + gridDim.x);
+    char* urow = ens + (f * G + (size_t)(y0 + g) * nx) * es;
+#pragma unroll
+    for (int m = 0; m < V; ++m)
+      store2(urow, 2 * (size_t)(t + T * m), make_float2(a[m].x + v[m].x, a[m].y + v[m].y), p.storage);
   }
 }
 
@@ -364,23 +377,45 @@ static cudaError_t row_fwd_LV(RowFwdParams p, int n_fields, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// rows per item of the inverse pass: the rows one CTA of at most 512 threads transforms at
+// once (a power of two dividing ny), halved while the tile, the row buffers and the stage
+// exceed 220 KB, and once more for the half schedule
+static RowShape inv_shape(int L, int V, int ny, int nx, int es, bool half) {
+  RowShape s;
+  s.T = L / V;
+  const int pow2 = ny & -ny;
+  int R = 512 / s.T;
+  if (R < 1) R = 1;
+  if (R > pow2) R = pow2;
+  auto smem = [&](int r) {
+    return (((size_t)L * r * sizeof(float2) + 127) & ~(size_t)127) +
+           (((size_t)r * row_pitch(L) * sizeof(float2) + 127) & ~(size_t)127) + (size_t)r * nx * es + 32;
+  };
+  while (R > 1 && smem(R) > 220 * 1024) R >>= 1;
+  if (half && R > 1) R >>= 1;
+  s.R = R;
+  s.LPC = R;
+  s.smem = smem(R);
+  return s;
+}
+
 template <int L, int V>
 static cudaError_t row_inv_LV(RowInvParams p, int n_fields, cudaStream_t st) {
   const int es = p.storage == kBF16 ? 2 : 4;
-  RowShape s = row_shape(L, V, p.ny, p.nx, es, 1, (p.vsel & 2) != 0);
-  if (s.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  RowShape s = inv_shape(L, V, p.ny, p.nx, es, (p.vsel & 2) != 0);
+  if (s.smem > 227 * 1024 || s.T * s.R > 512) return cudaErrorInvalidConfiguration;
   p.R = s.R;
   p.n_tiles = p.ny / s.R;
   auto kern = row_inv_kernel<L, V>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.T * s.LPC, s.smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.T * s.R, s.smem);
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)n_fields * p.n_tiles;
   const long long cap = (long long)sm_count() * per_sm;
   if (grid > cap) grid = cap;
-  kern<<<(unsigned)grid, s.T * s.LPC, s.smem, st>>>(p);
+  kern<<<(unsigned)grid, s.T * s.R, s.smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -414,6 +449,22 @@ bool row_line_supported(int n) {
     FFTENKF_ROW_SIZES(CASE)
 #undef CASE
     default: return false;
+  }
+}
+
+template <int L>
+static int row_inv_rows_L(int vsel, int ny, int nx, int es) {
+  const int V = (vsel & 1) ? plan_V(L, 1) : plan_V(L, 0);
+  RowShape s = inv_shape(L, V, ny, nx, es, (vsel & 2) != 0);
+  return (s.smem > 227 * 1024 || s.T * s.R > 512) ? 0 : s.R;
+}
+
+int row_inv_rows(int L, int vsel, int ny, int nx, int es) {
+  switch (L) {
+#define CASE(n) case n: return row_inv_rows_L<n>(vsel, ny, nx, es);
+    FFTENKF_ROW_SIZES(CASE)
+#undef CASE
+    default: return 0;
   }
 }
 

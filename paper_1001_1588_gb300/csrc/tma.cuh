@@ -70,6 +70,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// Per-thread asynchronous copies global -> shared of 8 bytes (cp.async), grouped
+// with commit and awaited with wait_group 0 (a hardware wait, no spin).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // CTA-wide wait for `parity` of `bar`, observed by thread 0.  Returns false
 // (for every thread) after a timeout; the caller must then return.
 __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status, int* flag) {

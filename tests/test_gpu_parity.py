@@ -127,6 +127,22 @@ def test_rhat_limits_gpu():
         assert gu.rel_l2(ua[0, k], p.data[0]) <= TOL32
 
 
+def test_vanishing_denominator_keeps_forecast():
+    """rhat = 0 and an observed block whose members are all equal: chat^(oo) = 0 and
+    chat^(jo) = 0 at every wavenumber, so every denominator chat^(oo) + rhat is 0 and
+    the gain is 0 (no information): the forecast is returned unchanged, as the oracle
+    does.  Exercises the zero-denominator branch of the gain."""
+    p = fields.make_config2(ny=64, nx=64)
+    o = int(np.flatnonzero(p.observed)[0])
+    p.ensemble[o, :] = p.ensemble[o, 0]
+    p.rhat[:] = 0.0
+    ua, st = _gu().gpu_analyze(p)
+    assert st == 0
+    ref = _oracle(p)
+    np.testing.assert_array_equal(ref, p.ensemble.astype(np.float64))
+    np.testing.assert_array_equal(ua, p.ensemble.astype(np.float64))
+
+
 def test_golden_shift_closed_form_16():
     """The two-block worked example of tests/golden/two_block_shift.json on a 16 x 16 grid.
 
