@@ -58,6 +58,11 @@ struct fftenkf_plan_s {
   float2* d_tw = nullptr;     // [L] row twiddles, [ny] column twiddles, [L+1] real-FFT twiddles
   int* d_status = nullptr;
   cudaStream_t aux = nullptr;
+  // tensor map of the increment spectra for the inverse row pass, cached for one workspace
+  alignas(64) CUtensorMap tm;
+  float2* tm_S = nullptr;
+  int tm_R = 0;
+  bool tm_ok = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // workspace layout (byte offsets)
   size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, off_rhat_t, ws_bytes;
@@ -392,8 +397,6 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   }
   up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
-  up.RS = row_inv_rows(p->L, p->sched[kPassRowInv], p->ny, p->nx, p->storage == FFTENKF_BF16 ? 2 : 4);
-  if (up.RS == 0 && e == cudaSuccess) e = cudaErrorInvalidConfiguration;
   up.vsel = p->sched[kPassUpdate];
   up.twY = p->twY(up.vsel); up.status = p->d_status;
   prof_begin(p, kPassUpdate, s);
@@ -403,7 +406,18 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   memset(&ip, 0, sizeof(ip));
   ip.ny = p->ny; ip.nx = p->nx; ip.L = p->L; ip.M = p->M; ip.N = p->N; ip.storage = p->storage;
   ip.vsel = p->sched[kPassRowInv];
-  ip.in = up.S; ip.ens = ensemble; ip.twL = p->twL(ip.vsel & 1); ip.twX = p->twX(); ip.status = p->d_status;
+  ip.ens = ensemble; ip.twL = p->twL(ip.vsel & 1); ip.twX = p->twX(); ip.status = p->d_status;
+  ip.R = row_inv_rows(p->L, ip.vsel, p->ny, p->nx, p->storage == FFTENKF_BF16 ? 2 : 4);
+  // columns per tensor copy: the largest divisor of L that is at most 256
+  ip.box_cols = p->L < 256 ? p->L : 256;
+  while (p->L % ip.box_cols) --ip.box_cols;
+  if (p->tm_S != up.S || p->tm_R != ip.R) {   // re-encoded when the workspace or the item rows change
+    p->tm_ok = encode_increment_map(&p->tm, up.S, p->M * p->N, p->ny, p->L, ip.R, ip.box_cols);
+    p->tm_S = up.S;
+    p->tm_R = ip.R;
+  }
+  if (!p->tm_ok && e == cudaSuccess) return fail(FFTENKF_ECUDA, "analyze: tensor map of the increment spectra refused");
+  ip.tm_in = p->tm;
   prof_begin(p, kPassRowInv, s);
   if (e == cudaSuccess) e = launch_row_inv(ip, p->M * p->N, s);
   prof_end(p, kPassRowInv, s);

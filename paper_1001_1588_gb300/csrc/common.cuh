@@ -10,6 +10,7 @@
 // .x or the .y part of packed column 0, so every wavenumber column k_x in
 // [0, nx/2] is one line of length ny.
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -82,9 +83,10 @@ struct RowFwdParams {
 
 struct RowInvParams {
   int ny, nx, L, R, M, N, storage, n_tiles;
-  // row spectra of the increments, field j*N+k, tiled: [field][ny/R][L][R] (R = rows per
-  // item of the inverse pass, row_inv_rows), so that one item is one contiguous block
-  const float2* in;
+  int box_cols;           // columns per tensor copy of the increment spectra (divides L, at most 256)
+  // row spectra of the increments, field j*N+k, [field][L][ny]; read through tm_in, the
+  // float32 view {2 ny, L, fields} with box {2 R, box_cols, 1} (R rows of box_cols columns)
+  alignas(64) CUtensorMap tm_in;
   void* ens;              // [M][N][ny][nx], updated in place
   const float2* twL;
   const float2* twX;
@@ -116,8 +118,7 @@ struct ColUpdParams {
   const float2* W;        // innovation row spectra, field k*n_obs+i
   const float* goo;       // [n_obs][L+1][ny]
   const float2* gjo;      // [n_obs*n_un][L+1][ny], table i*n_un+u
-  float2* S;              // increment row spectra, field j*N+k, tiled [ny/RS][L][RS]
-  int RS;                 // rows per tile of S (a power of two dividing ny)
+  float2* S;              // increment row spectra, field j*N+k
   const float2* twY;
   int* status;
   int n_stages;           // innovation prefetch stages (set by the launcher)
@@ -141,6 +142,9 @@ cudaError_t launch_row_fwd(const RowFwdParams& p, int n_fields, cudaStream_t s);
 cudaError_t launch_row_inv(const RowInvParams& p, int n_fields, cudaStream_t s);
 // rows per item of the inverse row pass for (nx/2, schedule, ny, nx, storage bytes); 0 = unsupported
 int row_inv_rows(int L, int vsel, int ny, int nx, int es);
+// tensor map of the increment row spectra [fields][L][ny] for the inverse row pass's tile
+// loads (R rows x box_cols columns per copy); false if R < 2 or the driver refuses it
+bool encode_increment_map(CUtensorMap* out, const float2* S, int fields, int ny, int L, int R, int box_cols);
 cudaError_t launch_col_stats(const ColStatsParams& p, cudaStream_t s);
 cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s);
 cudaError_t launch_gain(const GainParams& p, cudaStream_t s);

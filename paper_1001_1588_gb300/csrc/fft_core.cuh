@@ -69,6 +69,8 @@ __host__ __device__ constexpr int plan_V(int N, int sel) {
 // of the Stockham stages on distinct 8-byte banks
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
+// slots of a column pass's line buffer: a padded line rounded up to 16 slots (128 bytes)
+__host__ __device__ constexpr int col_line_slots(int N) { return (padded_len(N) + 15) & ~15; }
 // pitch of the staged rows of the row passes: a padded line rounded to 2 (mod 8) slots, so
 // that reading two rows x four columns per half-warp hits 16 distinct 8-byte banks
 __host__ __device__ constexpr int row_pitch(int N) { return padded_len(N) + ((10 - padded_len(N) % 8) % 8); }

@@ -1,5 +1,9 @@
 // Column-pass launchers: shared-memory sizing and dispatch on the number of
 // observed blocks (one translation unit per instantiation, compiled in parallel).
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "k_cols.cuh"
 
 namespace fftenkf {
@@ -13,6 +17,29 @@ int sm_count() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+// S [fields][L][ny] viewed as float32 {2 ny, L, fields}; a box is R consecutive k_y of
+// box_cols consecutive columns of one field, landing in shared memory as [box_cols][R]
+bool encode_increment_map(CUtensorMap* out, const float2* S, int fields, int ny, int L, int R, int box_cols) {
+  if (R < 2 || box_cols < 1 || box_cols > 256 || L % box_cols) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * ny, (cuuint64_t)L, (cuuint64_t)fields};
+  const cuuint64_t strides[2] = {(cuuint64_t)ny * sizeof(float2), (cuuint64_t)L * ny * sizeof(float2)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * R), (cuuint32_t)box_cols, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(S), dims, strides, box, estride,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static size_t padded_bytes(int ny) { return (size_t)((padded_len(ny) + 1) & ~1) * sizeof(float2); }
@@ -36,7 +63,7 @@ size_t col_update_smem(int ny, int n_obs, int vsel, int* lpc, int* n_stages) {
   const int T = ny / V;
   const size_t lines = (size_t)n_obs * ny * sizeof(float2);
   for (int nst = 2; nst >= 1; --nst) {
-    const size_t per = (nst + 1) * lines + padded_bytes(ny);
+    const size_t per = (nst + 1) * lines + (size_t)col_line_slots(ny) * sizeof(float2);
     int n = 256 / T;
     if (n < 1) n = 1;
     while (n > 1 && n * per + 32 > 200 * 1024) n >>= 1;

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
 template <int NY, int V, int NOBS>
 __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kernel(const ColUpdParams p) {
   constexpr int T = NY / V;
-  constexpr int PL = (padded_len(NY) + 1) & ~1;
+  constexpr int PL = col_line_slots(NY);
   extern __shared__ __align__(128) unsigned char smraw[];
   const int LPC = blockDim.x / T;
   const int g = threadIdx.x / T;
@@ -377,24 +377,14 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
       }
       fft_line<NY, V, true>(sv, xbuf, t, p.twY, line_bar<T>(g));
       if (active) {
-        // tiled increment spectra: k_y = RS y_t + r at [y_t][col][r]; RS consecutive k_y of a
-        // warp's stores fill one 8 RS-byte segment
-        float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * p.RS;
-        const size_t tstride = (size_t)p.L * p.RS;
-        const int rs = __ffs(p.RS) - 1;
+        float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * NY + t;
         if (part == 0) {
 #pragma unroll
-          for (int m = 0; m < V; ++m) {
-            const int ky = t + T * m;
-            dst[(size_t)(ky >> rs) * tstride + (ky & (p.RS - 1))] = sv[m];
-          }
+          for (int m = 0; m < V; ++m) dst[T * m] = sv[m];
         } else {
           float* d1 = reinterpret_cast<float*>(dst) + (part == 1 ? 0 : 1);
 #pragma unroll
-          for (int m = 0; m < V; ++m) {
-            const int ky = t + T * m;
-            d1[2 * ((size_t)(ky >> rs) * tstride + (ky & (p.RS - 1)))] = sv[m].x;
-          }
+          for (int m = 0; m < V; ++m) d1[2 * T * m] = sv[m].x;
         }
       }
     }

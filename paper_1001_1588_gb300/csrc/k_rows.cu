@@ -221,14 +221,14 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
 }
 
 // Inverse row pass.  A work item is R rows of one field (R = the rows the CTA
-// transforms at once); its increment spectra are one contiguous tile [L][R] of the
-// tiled layout written by the column update, brought in by one bulk copy while the
+// transforms at once); its increment spectra (R consecutive k_y of every column of
+// the column-major row spectra) arrive as a tile [L][R] by tensor copies while the
 // previous item is transformed, and its forecast rows by one bulk copy into a
 // stage.  The inverse real-FFT twist runs cooperatively over the tile, a pair of
 // columns c, L - c per step, and stages each row in its padded line buffer, which
 // then serves as that row's FFT exchange buffer.
 template <int L, int V>
-__global__ void __launch_bounds__(512, 1) row_inv_kernel(const RowInvParams p) {
+__global__ void __launch_bounds__(512, 1) row_inv_kernel(const __grid_constant__ RowInvParams p) {
   constexpr int T = L / V;
   constexpr int pitch = row_pitch(L);
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -249,9 +249,11 @@ __global__ void __launch_bounds__(512, 1) row_inv_kernel(const RowInvParams p) {
   const long long Q = (long long)p.M * p.N * p.n_tiles;   // item q = field q / n_tiles, tile q mod n_tiles
   char* ens = reinterpret_cast<char*>(p.ens);
 
-  auto issue_tile = [&](long long q) {
+  auto issue_tile = [&](long long q) {   // R k_y of every column of item q's field -> tile [L][R]
+    const int f = (int)(q / p.n_tiles);
+    const int y0 = (int)(q - (long long)f * p.n_tiles) * R;
     mbar_arrive_expect_tx(&bars[0], tile_bytes);
-    bulk_g2s(tile, p.in + (size_t)q * L * R, tile_bytes, &bars[0]);
+    for (int cb = 0; cb < L; cb += p.box_cols) tensor_load_3d(tile + (size_t)cb * R, &p.tm_in, 2 * y0, cb, f, &bars[0]);
   };
   auto issue_rows = [&](long long q) {
     const size_t f = q / p.n_tiles;
@@ -332,7 +334,8 @@ struct RowShape {
 };
 
 // rows per tile R (a power of two dividing ny), rows per round LPC, and the
-// shared memory: R staged rows plus one round of n_in input rows
+// shared memory: R staged rows plus one round of n_in input rows.  The half
+// schedule halves both, so that two CTAs of half the threads share an SM.
 static RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in, bool half) {
   RowShape s;
   s.T = L / V;
@@ -342,7 +345,7 @@ static RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in, bool h
   if (R > pow2) R = pow2;
   if (half && R > 2) R >>= 1;
   for (;;) {
-    int LPC = 512 / s.T;
+    int LPC = (half ? 256 : 512) / s.T;
     if (LPC < 1) LPC = 1;
     if (LPC > R) LPC = R;
     const size_t lines = ((size_t)R * row_pitch(L) * sizeof(float2) + 127) & ~(size_t)127;
@@ -387,12 +390,13 @@ static RowShape inv_shape(int L, int V, int ny, int nx, int es, bool half) {
   int R = 512 / s.T;
   if (R < 1) R = 1;
   if (R > pow2) R = pow2;
+  if (R > 128) R = 128;   // a tensor copy's box rows (2 R floats) are at most 256
   auto smem = [&](int r) {
     return (((size_t)L * r * sizeof(float2) + 127) & ~(size_t)127) +
            (((size_t)r * row_pitch(L) * sizeof(float2) + 127) & ~(size_t)127) + (size_t)r * nx * es + 32;
   };
-  while (R > 1 && smem(R) > 220 * 1024) R >>= 1;
-  if (half && R > 1) R >>= 1;
+  while (R > 2 && smem(R) > 220 * 1024) R >>= 1;
+  if (half && R > 2) R >>= 1;
   s.R = R;
   s.LPC = R;
   s.smem = smem(R);
@@ -403,8 +407,7 @@ template <int L, int V>
 static cudaError_t row_inv_LV(RowInvParams p, int n_fields, cudaStream_t st) {
   const int es = p.storage == kBF16 ? 2 : 4;
   RowShape s = inv_shape(L, V, p.ny, p.nx, es, (p.vsel & 2) != 0);
-  if (s.smem > 227 * 1024 || s.T * s.R > 512) return cudaErrorInvalidConfiguration;
-  p.R = s.R;
+  if (s.R != p.R || s.smem > 227 * 1024 || s.T * s.R > 512) return cudaErrorInvalidConfiguration;
   p.n_tiles = p.ny / s.R;
   auto kern = row_inv_kernel<L, V>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
@@ -456,7 +459,8 @@ template <int L>
 static int row_inv_rows_L(int vsel, int ny, int nx, int es) {
   const int V = (vsel & 1) ? plan_V(L, 1) : plan_V(L, 0);
   RowShape s = inv_shape(L, V, ny, nx, es, (vsel & 2) != 0);
-  return (s.smem > 227 * 1024 || s.T * s.R > 512) ? 0 : s.R;
+  // tensor copies need R >= 2 (16-byte rows of the box)
+  return (s.R < 2 || s.smem > 227 * 1024 || s.T * s.R > 512) ? 0 : s.R;
 }
 
 int row_inv_rows(int L, int vsel, int ny, int nx, int es) {

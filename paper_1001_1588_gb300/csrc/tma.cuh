@@ -70,13 +70,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// Per-thread asynchronous copies global -> shared of 8 bytes (cp.async), grouped
-// with commit and awaited with wait_group 0 (a hardware wait, no spin).
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+// Tensor load global -> shared of one 3-D box (coordinates innermost first, the
+// innermost one a multiple of 16 bytes), completed on an mbarrier like bulk_g2s.
+// The shared destination must be 128-byte aligned.
+__device__ __forceinline__ void tensor_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // CTA-wide wait for `parity` of `bar`, observed by thread 0.  Returns false
 // (for every thread) after a timeout; the caller must then return.
