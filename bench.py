@@ -41,7 +41,7 @@ WORKLOAD = "FFT EnKF analysis, 4 blocks 4096x4096, N=20, BF16 storage, 2 observe
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ny", type=int, default=NY)
@@ -116,7 +116,7 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "50"]
             if self.gpu_id is not None:
                 cmd += ["-i", str(self.gpu_id)]
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
@@ -130,6 +130,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def begin(self):
+        """Wait (at most 3 s) until the sampler produces lines; only later samples are summarised."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < 3.0:
+            time.sleep(0.02)
+        self.first = len(self.lines)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -141,7 +148,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "first", 0):]:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -282,6 +289,7 @@ def run_ours(a):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(gpu_id) as clk:
+        clk.begin()
         start.record(stream)
         for _ in range(a.steps):
             step()
@@ -427,6 +435,7 @@ def run_batched(a):
         raise RuntimeError("batched device status: %s" % abi.fftenkf_last_error())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(None) as clk:
+        clk.begin()
         e0.record(stream)
         for _ in range(a.steps):
             step()
