@@ -41,7 +41,7 @@ WORKLOAD = "FFT EnKF analysis, 4 blocks 4096x4096, N=20, BF16 storage, 2 observe
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ny", type=int, default=NY)
@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft (cuFFT) reference timing")
     ap.add_argument("--workload", default="large", choices=["large", "batched"],
                     help="large: 4 blocks 4096^2 N=20 (default, the headline); batched: 256 mixed analyses")
     ap.add_argument("--batch", type=int, default=256)
@@ -101,6 +102,54 @@ def analysis_bytes(ny, nx, M, N, n_obs, s):
     n_un = M - n_obs
     return (2 * M * N * G * s + n_obs * N * G * s + n_obs * N * G * s + n_obs * G * 4 + n_obs * K * 8
             + 2 * (n_obs * K * 4 + n_un * n_obs * K * 8) + M * N * G * s + (2 * M * N + n_obs * N) * 2 * K * 8)
+
+
+# ------------------------------------------------------------ cuFFT reference point
+def cufft_reference(ny, nx, M_, N_, n_obs, dev, steps=3, chunk=20):
+    """Time of the analysis's 2-D real transforms alone through torch.fft (cuFFT), FP32:
+    (M + n_obs) N forward R2C and M N inverse C2R transforms of ny x nx, in batches of `chunk`
+    fields, no other work.  A reference point, not this library's path."""
+    import torch
+    x = torch.randn(chunk, ny, nx, device=dev)
+    X = torch.fft.rfft2(x)
+    n_fwd, n_inv = (M_ + n_obs) * N_, M_ * N_
+
+    def one():
+        for _ in range(n_fwd // chunk):
+            torch.fft.rfft2(x, out=X)
+        for _ in range(n_inv // chunk):
+            torch.fft.irfft2(X, s=(ny, nx), out=x)
+
+    one()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    del x, X
+    return {"ms_per_step": ms, "transforms": n_fwd + n_inv, "dtype": "f32",
+            "note": "torch.fft rfft2/irfft2 (cuFFT) of the analysis's %d forward and %d inverse transforms in "
+                    "batches of %d fields; transforms only (no mean, statistics, gains, BF16 I/O)"
+                    % (n_fwd, n_inv, chunk)}
+
+
+# ------------------------------------------------------------ multi-rank reduction
+def max_over_ranks(value, dist_mod=None, device=None):
+    """The largest of every rank's value: a job's time is its slowest rank's."""
+    if dist_mod is None or not dist_mod.is_initialized() or dist_mod.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job rate: every rank's units over the slowest rank's time (weak scaling)."""
+    return float(units_per_rank) * world / (ms / 1e3)
 
 
 # ------------------------------------------------------------ clocks
@@ -300,12 +349,8 @@ def run_ours(a):
     ms = start.elapsed_time(stop)
     times = abi.fftenkf_pass_times(plan.handle)
     abi.fftenkf_set_profiling(plan.handle, False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    units = float(ny) * nx * Nm * a.steps * world
-    value = units / (ms / 1e3)
+    ms = max_over_ranks(ms, dist if world > 1 else None, dev)
+    value = job_throughput(float(ny) * nx * Nm * a.steps, world, ms)
 
     # roofline of the dominant pass
     s = 2
@@ -359,14 +404,14 @@ def run_ours(a):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": float(ny) * nx * Nm * a.e2e_steps * world / (ems / 1e3), "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
+        e2e = {"value": job_throughput(float(ny) * nx * Nm * a.e2e_steps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": a.e2e_steps,
                "ms_per_step": ems / a.e2e_steps}
+
+    cufft = None
+    if rank == 0 and not a.no_cufft:
+        cufft = cufft_reference(ny, nx, M, Nm, N_OBS, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -395,6 +440,7 @@ def run_ours(a):
             "e2e": e2e,
             "gpu_launches": 7 * a.steps,
             "cpu_baseline": cpu,
+            "cufft_reference": cufft,
             "source_sha": source_sha(),
         }
         print(json.dumps(out))
