@@ -49,6 +49,24 @@ __device__ __forceinline__ float2 load2(const void* base, size_t idx, int storag
   return *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base) + idx);
 }
 
+// the same with the storage type fixed at compile time
+template <int ST>
+__device__ __forceinline__ float2 load2(const void* base, size_t idx) {
+  if constexpr (ST == kBF16) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(reinterpret_cast<const __nv_bfloat16*>(base) + idx));
+  } else {
+    return *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base) + idx);
+  }
+}
+template <int ST>
+__device__ __forceinline__ void store2(void* base, size_t idx, float2 v) {
+  if constexpr (ST == kBF16) {
+    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base) + idx) = __float22bfloat162_rn(v);
+  } else {
+    *reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + idx) = v;
+  }
+}
+
 __device__ __forceinline__ void store2(void* base, size_t idx, float2 v, int storage) {
   if (storage == kBF16) {
     *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base) + idx) =
