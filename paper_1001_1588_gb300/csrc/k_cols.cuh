@@ -54,15 +54,20 @@ static __device__ __noinline__ bool gains_fp64(float* goo, float2* gjo, float2* 
   return ok;
 }
 
+// A column line into the canonical registers.  part 1 / 2: the real DC column (.x of the
+// packed column 0) or the real Nyquist column (.y); the branch is taken once per line.
 template <int NY, int V>
 __device__ __forceinline__ void read_line(float2 (&v)[V], const float2* __restrict__ src, int t, int part) {
   constexpr int T = NY / V;
+  if (part == 0) {
 #pragma unroll
-  for (int m = 0; m < V; ++m) {
-    float2 a = src[t + T * m];
-    if (part == 1) a = make_float2(a.x, 0.f);
-    if (part == 2) a = make_float2(a.y, 0.f);
-    v[m] = a;
+    for (int m = 0; m < V; ++m) v[m] = src[t + T * m];
+  } else if (part == 1) {
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = make_float2(src[t + T * m].x, 0.f);
+  } else {
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = make_float2(src[t + T * m].y, 0.f);
   }
 }
 
