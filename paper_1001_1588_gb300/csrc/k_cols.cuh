@@ -150,7 +150,8 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
 #pragma unroll
             for (int m = 0; m < V; ++m) {
               ko[i][m] = v[m];
-              acc[i * NY + t + T * m] += v[m].x * v[m].x + v[m].y * v[m].y;
+              float& a = acc[i * NY + t + T * m];
+              a = fmaf(v[m].x, v[m].x, fmaf(v[m].y, v[m].y, a));
             }
           }
         }
@@ -162,10 +163,10 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
             float2* a = xacc + (size_t)(i * p.n_un + u) * NY + t;
 #pragma unroll
             for (int m = 0; m < V; ++m) {
-              const float2 cr = cmulc(v[m], ko[i][m]);
+              // o += v conj(ko), as two fused multiply-adds per component
               float2 o = a[T * m];
-              o.x += cr.x;
-              o.y += cr.y;
+              o.x = fmaf(v[m].x, ko[i][m].x, fmaf(v[m].y, ko[i][m].y, o.x));
+              o.y = fmaf(v[m].y, ko[i][m].x, fmaf(-v[m].x, ko[i][m].y, o.y));
               a[T * m] = o;
             }
           }
@@ -371,7 +372,11 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
           if (i < p.n_obs) {
             const float2* gp = gl + (size_t)i * NY + t;
 #pragma unroll
-            for (int m = 0; m < V; ++m) sv[m] = cadd(sv[m], cmul(gp[T * m], wv[i][m]));
+            for (int m = 0; m < V; ++m) {   // sv += G w, as two fused multiply-adds per component
+              const float2 gv = gp[T * m];
+              sv[m].x = fmaf(gv.x, wv[i][m].x, fmaf(-gv.y, wv[i][m].y, sv[m].x));
+              sv[m].y = fmaf(gv.x, wv[i][m].y, fmaf(gv.y, wv[i][m].x, sv[m].y));
+            }
           }
         }
       }
