@@ -80,7 +80,8 @@ def test_config3_shape_f32():
 @pytest.mark.parametrize(
     "ny,nx,N",
     [(16, 16, 3), (32, 64, 5), (48, 96, 7), (96, 96, 5), (64, 192, 4), (192, 128, 6), (24, 48, 2),
-     (384, 384, 3), (768, 256, 3), (32, 4096, 3), (4096, 32, 3), (1024, 1024, 3), (3072, 48, 2), (16, 6144, 2)],
+     (384, 384, 3), (768, 256, 3), (32, 4096, 3), (4096, 32, 3), (1024, 1024, 3), (3072, 48, 2), (16, 6144, 2),
+     (16, 8192, 2)],
 )
 def test_sizes_single_block(ny, nx, N):
     S = fields.se_spectrum(ny, nx, 3.0, 1.0)
