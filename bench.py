@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--nx", type=int, default=NX)
     ap.add_argument("--members", type=int, default=N)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft (cuFFT) reference timing")
@@ -372,42 +372,61 @@ def run_ours(a):
     B_alg = analysis_bytes(ny, nx, M, Nm, N_OBS, s)
     step_ms = ms / a.steps
 
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    # end to end through the public API with host buffers (pinned), copies inside the timed region:
+    # every step copies its inputs host -> device, analyzes, and copies its result back.  Steps are
+    # streamed as a user streaming analyses would: device inputs double-buffered, host -> device
+    # copies on one stream, the analysis on the compute stream, device -> host on a third, so
+    # that step i+1's input copy overlaps step i's analysis and result copy.
     e2e = None
     if not a.no_e2e and a.e2e_steps > 0:
-        h_ens = prob.ensemble.cpu().pin_memory()
-        h_data = prob.data.cpu().pin_memory()
-        h_pert = prob.perturbations.cpu().pin_memory()
-        h_rhat = prob.rhat.cpu().pin_memory()
-        h_out = torch.empty_like(h_ens).pin_memory()
-        d_ens, d_data = torch.empty_like(prob.ensemble), torch.empty_like(prob.data)
-        d_pert, d_rhat = torch.empty_like(prob.perturbations), torch.empty_like(prob.rhat)
-        bi = sum(t.numel() * t.element_size() for t in (h_ens, h_data, h_pert, h_rhat))
-        bo = h_out.numel() * h_out.element_size()
+        h_in = [t.cpu().pin_memory() for t in (prob.ensemble, prob.data, prob.perturbations, prob.rhat)]
+        h_out = [torch.empty_like(h_in[0]).pin_memory() for _ in range(2)]
+        d_in = [[torch.empty_like(t) for t in (prob.ensemble, prob.data, prob.perturbations, prob.rhat)]
+                for _ in range(2)]
+        bi = sum(t.numel() * t.element_size() for t in h_in)
+        bo = h_out[0].numel() * h_out[0].element_size()
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        for e in ev_out:
+            e.record(s_out)
 
-        def e2e_step():
-            d_ens.copy_(h_ens, non_blocking=True)
-            d_data.copy_(h_data, non_blocking=True)
-            d_pert.copy_(h_pert, non_blocking=True)
-            d_rhat.copy_(h_rhat, non_blocking=True)
-            plan.analyze(d_ens, d_data, d_pert, d_rhat)
-            h_out.copy_(d_ens, non_blocking=True)
+        def e2e_step(i):
+            b = i % 2
+            s_in.wait_event(ev_out[b])                 # the buffer's previous result has left
+            with torch.cuda.stream(s_in):
+                for dt, ht in zip(d_in[b], h_in):
+                    dt.copy_(ht, non_blocking=True)
+                ev_in[b].record(s_in)
+            stream.wait_event(ev_in[b])
+            plan.analyze(*d_in[b], stream=stream)
+            ev_done[b].record(stream)
+            s_out.wait_event(ev_done[b])
+            with torch.cuda.stream(s_out):
+                h_out[b].copy_(d_in[b][0], non_blocking=True)
+                ev_out[b].record(s_out)
 
-        e2e_step()
+        for i in range(2):
+            e2e_step(i)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(a.e2e_steps):
-            e2e_step()
+        e0.record(s_in)
+        for i in range(a.e2e_steps):
+            e2e_step(i)
+        stream.wait_event(ev_out[(a.e2e_steps - 1) % 2])
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ems = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
         e2e = {"value": job_throughput(float(ny) * nx * Nm * a.e2e_steps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": a.e2e_steps,
-               "ms_per_step": ems / a.e2e_steps}
+               "ms_per_step": ems / a.e2e_steps,
+               "pipeline": "inputs double-buffered on the device; host->device, analysis and device->host on "
+                           "three streams, step i+1's input copy overlapping step i"}
+        del d_in, h_in, h_out
 
     cufft = None
     if rank == 0 and not a.no_cufft:
