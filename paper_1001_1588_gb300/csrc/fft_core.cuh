@@ -226,7 +226,7 @@ __device__ __forceinline__ int line_bar(int g) {
 // applies the R-point DFT and writes x[(j/NS) NS R + (j mod NS) + r NS].
 // Thread t owns butterflies j = t + T b (b < V/R), whose inputs are its
 // canonical slots b + r V/R; the last stage's outputs land in canonical slots.
-template <int N, int V, int S, int NS, bool INV>
+template <int N, int V, int S, int NS, bool INV, bool TRAIL>
 struct Stage {
   static __device__ __forceinline__ void run(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw, int bid) {
     constexpr int R = radix_at(N, V, S);
@@ -262,22 +262,26 @@ struct Stage {
       line_sync<T>(bid);
 #pragma unroll
       for (int m = 0; m < V; ++m) v[m] = sm[pidx(t + T * m)];
-      line_sync<T>(bid);
-      Stage<N, V, S + 1, NS * R, INV>::run(v, sm, t, tw, bid);
+      // the buffer is written again by the next stage, or (after the last exchange) by the caller;
+      // without TRAIL the caller synchronises before it reuses the buffer
+      if constexpr (TRAIL || S + 2 < num_stages(N, V)) line_sync<T>(bid);
+      Stage<N, V, S + 1, NS * R, INV, TRAIL>::run(v, sm, t, tw, bid);
     }
   }
 };
 
 // Unnormalised line DFT, sign -1 (forward) or +1 (INV).  Every thread of the
 // CTA (bid 0) or of the line (bid = line_bar(g)) must call it: it synchronises
-// with line_sync(bid) when the plan has >1 stage.
+// with line_sync(bid) when the plan has >1 stage.  With TRAIL = false it returns
+// while other threads of the line may still read sm: the caller must pass a
+// barrier of those threads before anything writes sm again.
 // tw: the stage-major twiddle table of (N, V) described above (exp(-2 pi i e/N)
 // values).  sm: this line's padded buffer.
-template <int N, int V, bool INV>
+template <int N, int V, bool INV, bool TRAIL = true>
 __device__ __forceinline__ void fft_line(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw, int bid = 0) {
   static_assert(N % V == 0, "V must divide N");
   static_assert(num_stages(N, V) > 0, "no radix plan");
-  Stage<N, V, 0, 1, INV>::run(v, sm, t, tw, bid);
+  Stage<N, V, 0, 1, INV, TRAIL>::run(v, sm, t, tw, bid);
 }
 
 }  // namespace fftenkf

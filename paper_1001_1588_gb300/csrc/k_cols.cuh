@@ -142,7 +142,8 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
         if (l + 1 < lines_per_col) issue(cb, l + 1);
         else if (cb + col_step < ncol) issue(cb + col_step, 0);
       }
-      fft_line<NY, V, false>(v, line, t, p.twY, line_bar<T>(g));
+      // no trailing barrier: the buffer is next written after the next line's CTA-wide waits
+      fft_line<NY, V, false, false>(v, line, t, p.twY, line_bar<T>(g));
       if (b < p.n_obs) {
 #pragma unroll
         for (int i = 0; i < NOBS; ++i) {
@@ -335,7 +336,10 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
     for (int i = 0; i < NOBS; ++i) {
       if (i < p.n_obs) {
         read_line<NY, V>(wv[i], w + (size_t)i * NY, t, part);
-        fft_line<NY, V, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
+        if (i + 1 < p.n_obs)   // the next innovation's transform reuses xbuf at once
+          fft_line<NY, V, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
+        else                   // the gain wait below synchronises the CTA first
+          fft_line<NY, V, false, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
       } else {
 #pragma unroll
         for (int m = 0; m < V; ++m) wv[i][m] = make_float2(0.f, 0.f);
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
         if (j + 1 < p.M) issue_g(base, j + 1);
         else if (base + step < n_items) issue_g(base + step, 0);
       }
-      fft_line<NY, V, true>(sv, xbuf, t, p.twY, line_bar<T>(g));
+      fft_line<NY, V, true, false>(sv, xbuf, t, p.twY, line_bar<T>(g));   // next use follows a CTA-wide wait
       if (active) {
         float2* dst = p.S + ((size_t)j * p.N + k) * fstride + (size_t)col * NY + t;
         if (part == 0) {

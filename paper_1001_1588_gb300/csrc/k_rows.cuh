@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(512, 1) row_inv_kernel(const __grid_constant__
 #pragma unroll
     for (int m = 0; m < V; ++m) v[m] = line[pidx(t + T * m)];
     line_sync<T>(line_bar<T>(g));   // the row is read before the FFT reuses its buffer
-    fft_line<L, V, true>(v, line, t, p.twL, line_bar<T>(g));
+    fft_line<L, V, true, false>(v, line, t, p.twL, line_bar<T>(g));   // the buffer is next written after the waits below
     if (!cta_wait(&bars[1], rph, p.status, flag)) {
       if (threadIdx.x == 0) mbar_wait_bounded(&bars[0], tph);   // next tile may be landing
       return;
