@@ -272,6 +272,8 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   mp.G = (long long)p->ny * p->nx;
   mp.ens = ens;
   mp.mean = reinterpret_cast<float*>(ws + p->off_mean);
+  mp.status = p->d_status;
+  mp.vsel = p->sched[kPassMean];
   prof_begin(p, kPassMean, s);
   cudaError_t e = launch_mean(mp, s);
   prof_end(p, kPassMean, s);

@@ -81,6 +81,8 @@ struct MeanParams {
   long long G;            // grid points per field
   const void* ens;        // [M][N][G]
   float* mean;            // [M][G]
+  int* status;            // device status word (bounded waits of the staged kernel), or null
+  int vsel;               // schedule: 0 = 2 stages of 2048 points, 1 = 4 stages of 1024 points
 };
 
 struct RowFwdParams {

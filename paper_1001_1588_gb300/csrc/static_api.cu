@@ -131,6 +131,8 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble,
   mp.G = (long long)G;
   mp.ens = ensemble;
   mp.mean = reinterpret_cast<float*>(base + off_mean);
+  mp.status = status;
+  mp.vsel = 0;
   if (e == cudaSuccess) e = launch_mean(mp, s);
   RowFwdParams rp;
   memset(&rp, 0, sizeof(rp));
