@@ -11,7 +11,8 @@ domain shortcut, and are used to pin the spectral oracle:
     solved with a dense LU, where the block covariance C^(ab) = F* diag(c^(ab)) F
     is the circulant (stationary) covariance whose frequency diagonal is c^(ab),
     R = blockdiag(F* diag(rhat_o) F), H selects the observed blocks and, as in
-    Sec. 2.2, C^(o'o) = 0 for distinct observed blocks.
+    Sec. 2.2, C^(o'o) = 0 for distinct observed blocks (or the full covariance,
+    for the coupled variant).
 """
 
 from __future__ import annotations
@@ -58,10 +59,13 @@ def dense_analyze(
     cross: Dict[tuple, np.ndarray],
     rhat_full: Dict[int, np.ndarray],
     observed: Sequence[int],
+    neglect_observed_cross: bool = True,
 ) -> np.ndarray:
     """eq. (enkf) with the stationary block covariance built from full-grid tables.
 
-    auto[o], cross[(j,o)], rhat_full[o] are full-grid frequency diagonals."""
+    auto[o], cross[(j,o)], rhat_full[o] are full-grid frequency diagonals.  With
+    ``neglect_observed_cross`` (Sec. 2.2) C^(o'o) = 0 for distinct observed blocks;
+    without it cross[(o', o)] must be given for them and the full covariance is used."""
     ens = np.asarray(ens, dtype=np.float64)
     M, N, ny, nx = ens.shape
     G = ny * nx
@@ -74,7 +78,7 @@ def dense_analyze(
         for a in range(M):
             if a == o:
                 blk = circulant(auto[o])
-            elif observed[a]:
+            elif observed[a] and neglect_observed_cross:
                 continue                      # neglected mutual cross-covariance
             else:
                 blk = circulant(cross[(a, o)])
@@ -82,6 +86,10 @@ def dense_analyze(
     HCHt = np.zeros((nO * G, nO * G), dtype=np.complex128)
     for i, o in enumerate(obs):
         HCHt[i * G:(i + 1) * G, i * G:(i + 1) * G] = circulant(auto[o]) + circulant(rhat_full[o])
+        if not neglect_observed_cross:
+            for i2, o2 in enumerate(obs):
+                if o2 != o:
+                    HCHt[i2 * G:(i2 + 1) * G, i * G:(i + 1) * G] = circulant(cross[(o2, o)])
     if max(np.abs(CHt.imag).max(initial=0), np.abs(HCHt.imag).max(initial=0)) > 1e-9 * (
         np.abs(CHt).max(initial=1) + np.abs(HCHt).max(initial=1)
     ):
