@@ -161,6 +161,27 @@ const char* fftenkf_pass_name(int pass);
 fftenkf_status fftenkf_set_schedule(fftenkf_plan plan, const int* sched, int n);
 fftenkf_status fftenkf_get_schedule(fftenkf_plan plan, int* sched, int n);
 
+/* ---------------------------------------------------------------- coupled observed blocks
+ * coupled != 0: keep the cross-covariance between observed blocks instead of
+ * neglecting it (the rule of Sec. 2.2).  eq. (multi-enkf) with the stationary
+ * block covariance then gives per wavenumber k the gain of block j
+ *     K_j(k) = chat_{j,O}(k) (chat_{O,O}(k) + diag(rhat_O(k)))^-1,
+ * chat_{a,b} = 1/(N-1) sum_k ahat_k^(a) conj(ahat_k^(b)) (eq. dii, cov-multi-spectral),
+ * and u_k^(j),a = u_k^(j) + F^-1 sum_o K_{j,o} F(d_o + e_{k,o} - u_k^(o)) for every block,
+ * observed ones included.  The n_obs x n_obs bracket is inverted in FP64; where it is
+ * singular (rhat = 0 and det <= 1e-6 a11 a22) its rank-1 pseudo-inverse A / tr(A)^2 is
+ * used, and 0 where tr(A) = 0.  This generalises the paper, which derives the single
+ * observed block.
+ * Supported for one or two observed blocks when the column statistics (n_obs autos,
+ * the observed pair and the n_obs x n_unobserved crosses) fit in shared memory; EUNSUPPORTED
+ * otherwise (the plan keeps its mode).  The workspace grows (gains of every block);
+ * a plan-owned workspace is reallocated on the next call, a caller workspace must be
+ * resized from fftenkf_workspace_size.  With coupling fftenkf_estimate_spectrum writes,
+ * after the observed autos, for every observed o (ascending) chat^(jo) of every block
+ * j != o (ascending), and fftenkf_analyze does not accept a caller spectrum (EUNSUPPORTED).
+ * Not thread-safe against concurrent calls on the same plan. */
+fftenkf_status fftenkf_set_coupled(fftenkf_plan plan, int coupled);
+
 /* ---------------------------------------------------------------- batched
  * Many independent analyses of uneven sizes (the block-state method with one
  * fully observed block each, H = I, eq. spectral-enkf): every pass is one

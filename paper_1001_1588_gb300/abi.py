@@ -53,6 +53,7 @@ _SIGNATURES = [
     ("fftenkf_pass_count", ctypes.c_int, []),
     ("fftenkf_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("fftenkf_set_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("fftenkf_pass_name", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_plan_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(fftenkf_dims)]),
     ("fftenkf_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
@@ -190,6 +191,10 @@ def fftenkf_pass_times(plan):
 def fftenkf_set_schedule(plan, sched):
     arr = (ctypes.c_int * len(sched))(*[int(x) for x in sched])
     check(lib().fftenkf_set_schedule(plan, arr, len(sched)), "fftenkf_set_schedule")
+
+
+def fftenkf_set_coupled(plan, coupled):
+    check(lib().fftenkf_set_coupled(plan, int(bool(coupled))), "fftenkf_set_coupled")
 
 
 def fftenkf_get_schedule(plan):

@@ -58,6 +58,8 @@ struct fftenkf_plan_s {
   float2* d_tw = nullptr;     // [L] row twiddles, [ny] column twiddles, [L+1] real-FFT twiddles
   int* d_status = nullptr;
   cudaStream_t aux = nullptr;
+  bool coupled = false;   // observed blocks coupled through their cross-covariance (n_obs <= 2)
+  int n_pair = 0;         // observed-pair tables in the column statistics (coupled: n_obs (n_obs-1) / 2)
   // tensor map of the increment spectra for the inverse row pass, cached for one workspace
   alignas(64) CUtensorMap tm;
   float2* tm_S = nullptr;
@@ -130,6 +132,26 @@ static void host_stage_twiddles(std::vector<float2>& out, int n, int V) {
   if (out.size() - base != (size_t)twiddle_count(n, V)) out.resize(base + twiddle_count(n, V));
 }
 
+// covariance tables per wavenumber in the column statistics
+static int table_floats(const fftenkf_plan_s* p) { return p->n_obs + 2 * p->n_pair + 2 * p->n_obs * p->n_un; }
+
+// workspace layout (byte offsets); the gain region holds goo/gjo, or gall [M][n_obs] (complex) when coupled
+static void layout(fftenkf_plan_s* p) {
+  const size_t G = (size_t)p->ny * p->nx;
+  const size_t line = (size_t)p->L * p->ny * sizeof(float2);     // one field's row spectra
+  const size_t tab = (size_t)(p->L + 1) * p->ny;
+  const size_t gain_tables = p->coupled ? (size_t)p->M * p->n_obs : (size_t)p->n_obs * p->n_un;
+  size_t off = 0;
+  p->off_mean = off; off = round_up(off + (size_t)p->M * G * sizeof(float), 256);
+  p->off_A = off;    off = round_up(off + (size_t)p->M * p->N * line, 256);
+  p->off_chat = off; off = round_up(off + (size_t)table_floats(p) * tab * sizeof(float), 256);
+  p->off_W = off;    off = round_up(off + (size_t)p->N * p->n_obs * line, 256);
+  p->off_goo = off;  off = round_up(off + (size_t)p->n_obs * tab * sizeof(float), 256);
+  p->off_gjo = off;  off = round_up(off + gain_tables * tab * sizeof(float2), 256);
+  p->off_rhat_t = off; off = round_up(off + (size_t)p->n_obs * tab * sizeof(double), 256);
+  p->ws_bytes = off;
+}
+
 extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_dims* dims,
                                               const uint8_t* observed_mask) {
   g_last_error.clear();
@@ -172,19 +194,7 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
     delete p;
     return fail(FFTENKF_EUNSUPPORTED, "covariance tables per column exceed shared memory (reduce blocks or ny)");
   }
-  // workspace layout
-  const size_t G = (size_t)p->ny * p->nx;
-  const size_t line = (size_t)p->L * p->ny * sizeof(float2);     // one field's row spectra
-  const size_t tab = (size_t)(p->L + 1) * p->ny;
-  size_t off = 0;
-  p->off_mean = off; off = round_up(off + (size_t)p->M * G * sizeof(float), 256);
-  p->off_A = off;    off = round_up(off + (size_t)p->M * p->N * line, 256);
-  p->off_chat = off; off = round_up(off + (size_t)nf * tab * sizeof(float), 256);
-  p->off_W = off;    off = round_up(off + (size_t)p->N * p->n_obs * line, 256);
-  p->off_goo = off;  off = round_up(off + (size_t)p->n_obs * tab * sizeof(float), 256);
-  p->off_gjo = off;  off = round_up(off + (size_t)p->n_obs * p->n_un * tab * sizeof(float2), 256);
-  p->off_rhat_t = off; off = round_up(off + (size_t)p->n_obs * tab * sizeof(double), 256);
-  p->ws_bytes = off;
+  layout(p);
   cudaGetDevice(&p->device);
   std::vector<float2> tw;
   for (int sel = 0; sel < 2; ++sel) {
@@ -240,7 +250,8 @@ extern "C" fftenkf_status fftenkf_workspace_size(fftenkf_plan p, size_t* bytes) 
 extern "C" fftenkf_status fftenkf_spectrum_size(fftenkf_plan p, size_t* n) {
   if (!p || !n) return fail(FFTENKF_EINVAL, "null argument");
   const size_t K = (size_t)p->ny * (p->L + 1);
-  *n = (size_t)p->n_obs * K + (size_t)p->n_obs * p->n_un * 2 * K;
+  const size_t n_cplx = p->coupled ? (size_t)p->n_obs * (p->M - 1) : (size_t)p->n_obs * p->n_un;
+  *n = (size_t)p->n_obs * K + n_cplx * 2 * K;
   return FFTENKF_OK;
 }
 
@@ -301,6 +312,7 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   cp.goo = reinterpret_cast<float*>(ws + p->off_goo);
   cp.gjo = reinterpret_cast<float2*>(ws + p->off_gjo);
   cp.inv_G = (float)(1.0 / ((double)p->ny * (double)p->nx));
+  cp.n_pair = p->n_pair;
   cp.scale = (float)(1.0 / ((double)(p->N - 1) * (double)p->ny * (double)p->nx));
   cp.vsel = p->sched[kPassStats];
   cp.twY = p->twY(cp.vsel);
@@ -328,7 +340,8 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum(fftenkf_plan p, const void* 
   cudaError_t e = run_statistics(p, ensemble, ws, s, nullptr);
   prof_begin(p, kPassChatOut, s);
   if (e == cudaSuccess)
-    e = launch_chat_out(reinterpret_cast<float*>(ws + p->off_chat), spectrum_out, p->ny, p->L, p->n_obs, p->n_un, s);
+    e = launch_chat_out(reinterpret_cast<float*>(ws + p->off_chat), spectrum_out, p->ny, p->L,
+                        chat_out_map(p->n_obs, p->n_un, p->coupled ? 1 : 0, p->obs, p->un, p->M), s);
   prof_end(p, kPassChatOut, s);
   if (e != cudaSuccess) return cuda_fail(e, "estimate_spectrum");
   return FFTENKF_OK;
@@ -343,6 +356,8 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   if (!aligned(ensemble, 16) || !aligned(data, 16) || !aligned(perturbations, 16) || !aligned(rhat, 16) ||
       (spectrum && !aligned(spectrum, 16)))
     return fail(FFTENKF_EINVAL, "pointers must be 16-byte aligned");
+  if (spectrum && p->coupled)
+    return fail(FFTENKF_EUNSUPPORTED, "a caller-supplied spectrum is not supported with coupled observed blocks");
   char* ws;
   fftenkf_status st = get_workspace(p, workspace, &ws);
   if (st != FFTENKF_OK) return st;
@@ -372,7 +387,22 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
     prof_end(p, kPassGain, p->aux);
   }
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
-  if (!spectrum) {
+  if (!spectrum && p->coupled) {
+    // tables of the column statistics, then the coupled gains (FP64 bracket inverse per wavenumber)
+    if (e == cudaSuccess) e = run_statistics(p, ensemble, ws, s, nullptr);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+    CoupledGainParams cg;
+    memset(&cg, 0, sizeof(cg));
+    cg.ny = p->ny; cg.L = p->L; cg.n_obs = p->n_obs; cg.n_un = p->n_un; cg.n_pair = p->n_pair;
+    cg.chat_t = reinterpret_cast<const float*>(ws + p->off_chat);
+    cg.rhat_t = rhat_t;
+    cg.gall = gp.gjo;
+    cg.inv_G = (float)(1.0 / ((double)p->ny * (double)p->nx));
+    cg.status = p->d_status;
+    prof_begin(p, kPassGain, s);
+    if (e == cudaSuccess) e = launch_coupled_gain(cg, s);
+    prof_end(p, kPassGain, s);
+  } else if (!spectrum) {
     // mean and anomaly rows need no rhat; the statistics pass (which forms the gains) waits for it
     if (e == cudaSuccess) e = run_statistics(p, ensemble, ws, s, rhat_t, p->ev_join);
   } else {
@@ -398,6 +428,8 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
     up.un_of_block[j] = p->un_of_block[j];
   }
   up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
+  up.coupled = p->coupled ? 1 : 0;
+  up.gall = gp.gjo;
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
   up.vsel = p->sched[kPassUpdate];
   up.twY = p->twY(up.vsel); up.status = p->d_status;
@@ -492,7 +524,7 @@ extern "C" const char* fftenkf_pass_name(int pass) {
 
 extern "C" fftenkf_status fftenkf_set_schedule(fftenkf_plan p, const int* sched, int n) {
   if (!p || !sched || n < 0) return fail(FFTENKF_EINVAL, "null argument");
-  const int nf = p->n_obs + 2 * p->n_obs * p->n_un;
+  const int nf = table_floats(p);
   int next[kPassCount];
   for (int a = 0; a < kPassCount; ++a) next[a] = (a < n) ? sched[a] : p->sched[a];
   for (int a = 0; a < kPassCount; ++a) {
@@ -504,6 +536,29 @@ extern "C" fftenkf_status fftenkf_set_schedule(fftenkf_plan p, const int* sched,
                        row_inv_rows(p->L, next[kPassRowInv], p->ny, p->nx, p->storage == FFTENKF_BF16 ? 2 : 4) == 0))
     return fail(FFTENKF_EUNSUPPORTED, "schedule does not fit in shared memory");
   for (int a = 0; a < kPassCount; ++a) p->sched[a] = next[a];
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_set_coupled(fftenkf_plan p, int coupled) {
+  g_last_error.clear();
+  if (!p) return fail(FFTENKF_EINVAL, "null argument");
+  const bool c = coupled != 0;
+  if (c && (p->n_obs < 1 || p->n_obs > 2))
+    return fail(FFTENKF_EUNSUPPORTED, "coupled observed blocks: one or two observed blocks supported");
+  const int n_pair = c ? p->n_obs * (p->n_obs - 1) / 2 : 0;
+  const int nf = p->n_obs + 2 * n_pair + 2 * p->n_obs * p->n_un;
+  if (p->n_obs > 0 && col_stats_smem(p->ny, nf, p->sched[kPassStats], nullptr) == 0)
+    return fail(FFTENKF_EUNSUPPORTED, "coupled covariance tables per column exceed shared memory (reduce blocks or ny)");
+  if (c == p->coupled) return FFTENKF_OK;
+  p->coupled = c;
+  p->n_pair = n_pair;
+  const size_t old_bytes = p->ws_bytes;
+  layout(p);
+  if (p->own_ws && p->ws_bytes > old_bytes) {   // reallocated on the next call
+    cudaFree(p->own_ws);
+    p->own_ws = nullptr;
+  }
+  p->tm_S = nullptr;   // the tensor map is encoded again for the new layout
   return FFTENKF_OK;
 }
 

@@ -129,7 +129,23 @@ struct ColStatsParams {
   const float2* twY;      // stage-major twiddles of the ny-point plan
   int* status;
   int vsel;
+  // coupled observed blocks (n_obs <= 2, tables only: rhat_t null): the complex tables start
+  // with n_pair = n_obs (n_obs - 1) / 2 observed-pair tables chat^(o1 o0)
+  int n_pair;
 };
+
+// Gains with coupled observed blocks (n_obs <= 2) from the column statistics' tables, per
+// wavenumber: K_r = chat_{r,O} (chat_OO + diag(rhat))^-1 for every block r in role order
+// (observed, then unobserved), scaled by 1/(ny nx), into gall [role][n_obs][L+1][ny].
+struct CoupledGainParams {
+  int ny, L, n_obs, n_un, n_pair;
+  const float* chat_t;    // [n_obs][L+1][ny] then complex [n_pair + n_obs n_un][L+1][ny]
+  const double* rhat_t;   // [n_obs][L+1][ny]
+  float2* gall;
+  float inv_G;
+  int* status;
+};
+cudaError_t launch_coupled_gain(const CoupledGainParams& p, cudaStream_t s);
 
 struct ColUpdParams {
   int ny, L, M, N, n_obs, n_un;
@@ -143,6 +159,8 @@ struct ColUpdParams {
   int* status;
   int n_stages;           // innovation prefetch stages (set by the launcher)
   int vsel;
+  int coupled;            // gains of every block j in gall [M][n_obs][L+1][ny] (complex)
+  const float2* gall;
 };
 
 struct GainParams {
@@ -168,7 +186,15 @@ bool encode_increment_map(CUtensorMap* out, const float2* S, int fields, int ny,
 cudaError_t launch_col_stats(const ColStatsParams& p, cudaStream_t s);
 cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s);
 cudaError_t launch_gain(const GainParams& p, cudaStream_t s);
-cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, int n_obs, int n_un,
+// output order of the complex spectrum tables: complex output q comes from complex
+// column-pass table src[q], conjugated where conj[q] is set
+struct ChatOutMap {
+  int n_auto, n_cplx;
+  int src[64];
+  int conj[64];
+};
+ChatOutMap chat_out_map(int n_obs, int n_un, int coupled, const int* obs, const int* un, int M);
+cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, const ChatOutMap& map,
                             cudaStream_t s);
 // rhat [n][ny][L+1] -> rhat_t [n][L+1][ny]
 cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s);

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
   const int LPC = blockDim.x / T;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
-  const int nf = p.n_obs + 2 * p.n_obs * p.n_un;
+  const int nf = p.n_obs + 2 * p.n_pair + 2 * p.n_obs * p.n_un;
   float* acc_all = reinterpret_cast<float*>(smraw);
   float* acc = acc_all + (size_t)g * nf * NY;
   float2* xacc = reinterpret_cast<float2*>(acc + p.n_obs * NY);
@@ -154,6 +154,16 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
               float& a = acc[i * NY + t + T * m];
               a = fmaf(v[m].x, v[m].x, fmaf(v[m].y, v[m].y, a));
             }
+            if (NOBS >= 2 && i == 1 && p.n_pair) {   // coupled: observed pair chat^(o1 o0) += v conj(ko_0)
+              float2* a = xacc + t;
+#pragma unroll
+              for (int m = 0; m < V; ++m) {
+                float2 o = a[T * m];
+                o.x = fmaf(v[m].x, ko[0][m].x, fmaf(v[m].y, ko[0][m].y, o.x));
+                o.y = fmaf(v[m].y, ko[0][m].x, fmaf(-v[m].x, ko[0][m].y, o.y));
+                a[T * m] = o;
+              }
+            }
           }
         }
       } else {
@@ -161,7 +171,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
 #pragma unroll
         for (int i = 0; i < NOBS; ++i) {
           if (i < p.n_obs) {
-            float2* a = xacc + (size_t)(i * p.n_un + u) * NY + t;
+            float2* a = xacc + (size_t)(p.n_pair + i * p.n_un + u) * NY + t;
 #pragma unroll
             for (int m = 0; m < V; ++m) {
               // o += v conj(ko), as two fused multiply-adds per component
@@ -181,6 +191,16 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
       // rhat values are requested E at a time before any of their tables is stored, so the
       // epilogue waits for one memory latency per E values rather than one per value
       constexpr int E = (V % 8 == 0) ? 8 : ((V % 4 == 0) ? 4 : V);
+      if (p.n_pair && p.chat) {   // coupled: the observed pair chat^(o1 o0), first complex table
+#pragma unroll
+        for (int m = 0; m < V; ++m) {
+          const int ky = t + T * m;
+          const float2 a = xacc[ky];
+          const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
+          bad |= !(isfinite(x.x) && isfinite(x.y));
+          xout[(size_t)c * NY + ky] = x;
+        }
+      }
 #pragma unroll 1
       for (int i = 0; i < p.n_obs; ++i) {
 #pragma unroll 1
@@ -219,10 +239,11 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
               }
             } else if (xout) {
               for (int u = 0; u < p.n_un; ++u) {
-                const float2 a = xacc[(size_t)(i * p.n_un + u) * NY + ky];
+                const int q = p.n_pair + i * p.n_un + u;
+                const float2 a = xacc[(size_t)q * NY + ky];
                 const float2 x = make_float2(a.x * p.scale, a.y * p.scale);
                 bad |= !(isfinite(x.x) && isfinite(x.y));
-                xout[(i * p.n_un + u) * tab + at] = x;
+                xout[q * tab + at] = x;
               }
             }
           }
@@ -277,7 +298,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
   // gain lines of target block j for every group's item: observed j -> one float line,
   // unobserved j -> n_obs complex lines
   auto issue_g = [&](long long base, int j) {
-    const int io = p.obs_of_block[j];
+    const int io = p.coupled ? -1 : p.obs_of_block[j];   // coupled: n_obs complex gains for every block
     const uint32_t line_bytes = (io >= 0) ? NY * sizeof(float) : NY * sizeof(float2);
     const int nl = (io >= 0) ? 1 : p.n_obs;
     int nvalid = 0;
@@ -290,6 +311,10 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
       float2* dst = gst + (size_t)gg * p.n_obs * NY;
       if (io >= 0) {
         bulk_g2s(dst, p.goo + io * tab + (size_t)c * NY, line_bytes, gbar);
+      } else if (p.coupled) {   // gall [role][n_obs]: observed blocks first, then unobserved
+        const int role = (p.obs_of_block[j] >= 0) ? p.obs_of_block[j] : p.n_obs + p.un_of_block[j];
+        for (int i = 0; i < p.n_obs; ++i)
+          bulk_g2s(dst + (size_t)i * NY, p.gall + (size_t)(role * p.n_obs + i) * tab + (size_t)c * NY, line_bytes, gbar);
       } else {
         const int u = p.un_of_block[j];
         for (int i = 0; i < p.n_obs; ++i)
@@ -355,7 +380,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
       }
       gph ^= 1;
       float2 sv[V];
-      const int io = p.obs_of_block[j];
+      const int io = p.coupled ? -1 : p.obs_of_block[j];
 #pragma unroll
       for (int m = 0; m < V; ++m) sv[m] = make_float2(0.f, 0.f);
       if (io >= 0) {
@@ -414,7 +439,7 @@ template <int NY, int V, int NOBS>
 inline cudaError_t col_stats_NYV(const ColStatsParams& p, cudaStream_t st) {
   constexpr int T = NY / V;
   int lpc = 1;
-  const int nf = p.n_obs + 2 * p.n_obs * p.n_un;
+  const int nf = p.n_obs + 2 * p.n_pair + 2 * p.n_obs * p.n_un;
   const size_t smem = col_stats_smem(NY, nf, p.vsel, &lpc);
   if (smem == 0) return cudaErrorInvalidConfiguration;
   auto kern = col_stats_kernel<NY, V, NOBS>;

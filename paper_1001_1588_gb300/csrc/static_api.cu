@@ -149,7 +149,8 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble,
   cp.scale = (float)(1.0 / ((double)(n_members - 1) * (double)ny * (double)nx));
   cp.twY = twY; cp.status = status; cp.vsel = 0;
   if (e == cudaSuccess) e = launch_col_stats(cp, s);
-  if (e == cudaSuccess) e = launch_chat_out(cp.chat, spectrum_out, ny, L, 1, 0, s);
+  const int block0 = 0;
+  if (e == cudaSuccess) e = launch_chat_out(cp.chat, spectrum_out, ny, L, chat_out_map(1, 0, 0, &block0, nullptr, 1), s);
   if (e != cudaSuccess) return sfail(FFTENKF_ECUDA, std::string("estimate_spectrum_static: ") + cudaGetErrorString(e));
   return FFTENKF_OK;
 }

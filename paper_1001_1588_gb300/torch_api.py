@@ -24,7 +24,7 @@ class Plan:
     """One (grid, blocks, members, storage, observed mask) configuration."""
 
     def __init__(self, ny: int, nx: int, n_blocks: int, n_members: int, storage: torch.dtype,
-                 observed: Sequence[int]):
+                 observed: Sequence[int], coupled: bool = False):
         if storage not in _STORAGE:
             raise TypeError("storage must be torch.float32 or torch.bfloat16")
         self.ny, self.nx, self.M, self.N = ny, nx, n_blocks, n_members
@@ -32,6 +32,13 @@ class Plan:
         self.observed = [int(bool(o)) for o in observed]
         self.n_obs = sum(self.observed)
         self.handle = abi.fftenkf_plan_create(ny, nx, n_blocks, n_members, _STORAGE[storage], self.observed)
+        if coupled:
+            try:
+                abi.fftenkf_set_coupled(self.handle, True)
+            except Exception:
+                self.close()
+                raise
+        self.coupled = bool(coupled)
         self.workspace_bytes = abi.fftenkf_workspace_size(self.handle)
         self.spectrum_doubles = abi.fftenkf_spectrum_size(self.handle)
         self._ws = None
