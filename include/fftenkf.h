@@ -110,6 +110,20 @@ fftenkf_status fftenkf_analyze(fftenkf_plan plan, void* ensemble, const float* d
                                const void* perturbations, const double* rhat, const double* spectrum,
                                void* workspace, void* stream);
 
+/* The same analysis with the perturbations e_{k,o} ~ N(0, R_o) drawn by the library
+ * (eq. enkf: the EnKF's data perturbations; R_o = F* diag(rhat_o) F) instead of passed in:
+ * in frequency space, ehat_{k,o} = sqrt(rhat_o) zhat_{k,o} with zhat the unitary DFT of a
+ * white N(0, 1) field (Hermitian, real at the self-conjugate wavenumbers), added to the
+ * innovation spectrum after its forward transform, so no perturbation field is stored or
+ * read.  zhat comes from the counter-based generator Philox4x32-10 (Salmon et al., SC 2011)
+ * with counter (k_y', k_x, k n_obs + o, 0) per half-spectrum wavenumber (k_y' = min(k_y,
+ * ny - k_y) in the columns k_x = 0 and nx/2), key `seed`, and Box-Muller on the top 24 bits
+ * of its first two words; the same seed gives the same analysis.  Other arguments, layouts
+ * and errors as fftenkf_analyze. */
+fftenkf_status fftenkf_analyze_seeded(fftenkf_plan plan, void* ensemble, const float* data, const double* rhat,
+                                      const double* spectrum, unsigned long long seed, void* workspace,
+                                      void* stream);
+
 /* Allocation-free estimate for one block (the paper has no counterpart: this
  * is a deployment variant of fftenkf_estimate_spectrum).  For callers that may
  * not call cudaMalloc -- e.g. a host framework that owns every device

@@ -13,8 +13,8 @@ ny - k_y, and k_y = 0, ny/2 are real N(0, 1).
 The normals come from the counter-based generator Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
 "Parallel random numbers: as easy as 1, 2, 3", SC 2011), counter
 (k_y', k_x, k n_obs + o, 0) with k_y' = min(k_y, ny - k_y) in the columns 0 and nx/2, key
-(seed mod 2^32, seed div 2^32); words 0 and 1 give u_i = (floor(w_i / 2^8) + 1/2) / 2^24 (exact
-in single precision) and Box-Muller
+(seed mod 2^32, seed div 2^32); words 0 and 1 give u_i = (floor(w_i / 2^8) + 1/2) / 2^24 and
+Box-Muller
 n_1 + i n_2 = sqrt(-2 ln u_1) exp(2 pi i u_2).  Complex entries are (n_1 + i n_2) / sqrt(2),
 real ones n_1.  The GPU implements the same definition independently.
 """

@@ -44,6 +44,7 @@ _SIGNATURES = [
     ("fftenkf_spectrum_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("fftenkf_estimate_spectrum", ctypes.c_int, [ctypes.c_void_p] * 5),
     ("fftenkf_analyze", ctypes.c_int, [ctypes.c_void_p] * 8),
+    ("fftenkf_analyze_seeded", ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_ulonglong] + [ctypes.c_void_p] * 2),
     ("fftenkf_estimate_spectrum_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("fftenkf_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -155,6 +156,11 @@ def fftenkf_estimate_spectrum(plan, ensemble, spectrum_out, workspace=None, stre
 def fftenkf_analyze(plan, ensemble, data, perturbations, rhat, spectrum=None, workspace=None, stream=None):
     check(lib().fftenkf_analyze(plan, _p(ensemble), _p(data), _p(perturbations), _p(rhat), _p(spectrum),
                                 _p(workspace), stream), "fftenkf_analyze")
+
+
+def fftenkf_analyze_seeded(plan, ensemble, data, rhat, seed, spectrum=None, workspace=None, stream=None):
+    check(lib().fftenkf_analyze_seeded(plan, _p(ensemble), _p(data), _p(rhat), _p(spectrum), int(seed),
+                                       _p(workspace), stream), "fftenkf_analyze_seeded")
 
 
 def fftenkf_estimate_spectrum_static(ensemble, ny, nx, n_members, storage, spectrum_out, stream=None):

@@ -347,13 +347,15 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum(fftenkf_plan p, const void* 
   return FFTENKF_OK;
 }
 
-extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const float* data, const void* perturbations,
-                                          const double* rhat, const double* spectrum, void* workspace, void* stream) {
+// the analysis with given perturbations, or (drawn) with perturbations drawn in frequency space
+static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* data, const void* perturbations,
+                                   const double* rhat, const double* spectrum, bool drawn, unsigned long long seed,
+                                   void* workspace, void* stream) {
   g_last_error.clear();
   if (!p || !ensemble) return fail(FFTENKF_EINVAL, "null argument");
   if (p->n_obs == 0) return FFTENKF_OK;   // nothing observed: the forecast is the analysis
-  if (!data || !perturbations || !rhat) return fail(FFTENKF_EINVAL, "null argument");
-  if (!aligned(ensemble, 16) || !aligned(data, 16) || !aligned(perturbations, 16) || !aligned(rhat, 16) ||
+  if (!data || (!perturbations && !drawn) || !rhat) return fail(FFTENKF_EINVAL, "null argument");
+  if (!aligned(ensemble, 16) || !aligned(data, 16) || (!drawn && !aligned(perturbations, 16)) || !aligned(rhat, 16) ||
       (spectrum && !aligned(spectrum, 16)))
     return fail(FFTENKF_EINVAL, "pointers must be 16-byte aligned");
   if (spectrum && p->coupled)
@@ -377,6 +379,11 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   gp.scale = (float)(1.0 / ((double)p->ny * (double)p->nx));
   gp.status = p->d_status;
   double* rhat_t = reinterpret_cast<double*>(ws + p->off_rhat_t);
+  if (spectrum && drawn) {   // the drawn perturbations scale by sqrt(rhat) in the column layout
+    prof_begin(p, kPassRhatT, p->aux);
+    if (e == cudaSuccess) e = launch_rhat_transpose(rhat, rhat_t, p->n_obs, p->ny, p->L, p->aux);
+    prof_end(p, kPassRhatT, p->aux);
+  }
   if (!spectrum) {
     prof_begin(p, kPassRhatT, p->aux);
     if (e == cudaSuccess) e = launch_rhat_transpose(rhat, rhat_t, p->n_obs, p->ny, p->L, p->aux);
@@ -411,7 +418,7 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   RowFwdParams rp;
   memset(&rp, 0, sizeof(rp));
   rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
-  rp.n_obs = p->n_obs; rp.mode = kInnovation; rp.storage = p->storage;
+  rp.n_obs = p->n_obs; rp.mode = drawn ? kInnovationDrawn : kInnovation; rp.storage = p->storage;
   for (int i = 0; i < p->n_obs; ++i) rp.obs[i] = p->obs[i];
   rp.ens = ensemble; rp.data = data; rp.pert = perturbations;
   rp.out = reinterpret_cast<float2*>(ws + p->off_W);
@@ -430,6 +437,10 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   up.W = rp.out; up.goo = gp.goo; up.gjo = gp.gjo;
   up.coupled = p->coupled ? 1 : 0;
   up.gall = gp.gjo;
+  up.drawn = drawn ? 1 : 0;
+  up.seed = seed;
+  up.rhat_t = rhat_t;
+  up.sqrt_G = (float)std::sqrt((double)p->ny * (double)p->nx);
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
   up.vsel = p->sched[kPassUpdate];
   up.twY = p->twY(up.vsel); up.status = p->d_status;
@@ -457,6 +468,17 @@ extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const 
   prof_end(p, kPassRowInv, s);
   if (e != cudaSuccess) return cuda_fail(e, "analyze");
   return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_analyze(fftenkf_plan p, void* ensemble, const float* data, const void* perturbations,
+                                          const double* rhat, const double* spectrum, void* workspace, void* stream) {
+  return analyze_impl(p, ensemble, data, perturbations, rhat, spectrum, false, 0, workspace, stream);
+}
+
+extern "C" fftenkf_status fftenkf_analyze_seeded(fftenkf_plan p, void* ensemble, const float* data, const double* rhat,
+                                                 const double* spectrum, unsigned long long seed, void* workspace,
+                                                 void* stream) {
+  return analyze_impl(p, ensemble, data, nullptr, rhat, spectrum, true, seed, workspace, stream);
 }
 
 extern "C" fftenkf_status fftenkf_last_device_status(fftenkf_plan p, void* stream) {

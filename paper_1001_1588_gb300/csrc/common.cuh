@@ -33,7 +33,9 @@ __device__ __forceinline__ float pair_div(float hi, float lo, float n, float inv
 constexpr int kMaxBlocks = 16;
 constexpr int kMaxObs = 4;
 
-enum RowMode { kAnomaly = 0, kInnovation = 1 };
+// innovation rows d - u + e with given perturbations, or d - u when the perturbations are drawn in
+// frequency space by the column update
+enum RowMode { kAnomaly = 0, kInnovation = 1, kInnovationDrawn = 2 };
 enum Storage { kF32 = 0, kBF16 = 1 };
 
 // Status bits written by kernels (OR-ed into the plan's device word).
@@ -161,6 +163,12 @@ struct ColUpdParams {
   int vsel;
   int coupled;            // gains of every block j in gall [M][n_obs][L+1][ny] (complex)
   const float2* gall;
+  // perturbations drawn here (seeded analysis): what_{k,o} += sqrt(ny nx) sqrt(rhat_o) zhat_{k,o},
+  // zhat from Philox4x32-10 per (wavenumber, stream k n_obs + o) under key `seed`
+  int drawn;
+  unsigned long long seed;
+  const double* rhat_t;   // [n_obs][L+1][ny]
+  float sqrt_G;
 };
 
 struct GainParams {

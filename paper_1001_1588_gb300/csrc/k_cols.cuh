@@ -22,17 +22,6 @@
 
 namespace fftenkf {
 
-// 1/x in FP64 for normal x > 0: the approximate reciprocal refined by two steps of
-// the Newton-Raphson iteration for f(y) = 1/y - x (e <- 1 - x y, y <- y + y e).
-__device__ __forceinline__ double recip64_ex(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
-
 // Gains of one wavenumber whose denominator chat^(oo) + rhat is below FLT_MIN (both
 // vanish): the quotients in FP64, 0 where the denominator is 0.  Kept out of line so
 // that the common FP32 path carries none of its instructions.  xa: the first cross
@@ -255,6 +244,45 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
   }
 }
 
+// ----------------------------------------------------------------- drawn perturbations
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two 32 x 32 -> 64-bit
+// products mixed with the other counter words and the key, the key advanced by the Weyl
+// increments after every round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// zhat(k_y, k_x) of one stream: the unitary DFT of a white N(0, 1) field on the half spectrum.
+// Counter (k_y', k_x, stream, 0), k_y' = min(k_y, ny - k_y) in the columns 0 and L so that they
+// are Hermitian in k_y; key = seed.  Words 0, 1 -> u = (w / 2^8 + 1/2) 2^-24 (single precision),
+// Box-Muller n1 + i n2; complex entries (n1 + i n2) / sqrt(2), self-conjugate ones n1.
+__device__ __forceinline__ float2 white_spectrum(unsigned long long seed, int stream, int ky, int kx, int ny, int L) {
+  const bool edge = (kx == 0) || (kx == L);
+  int kyc = ky;
+  if (edge) {
+    const int m = (ny - ky) % ny;
+    kyc = ky < m ? ky : m;
+  }
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)kyc, (uint32_t)kx, (uint32_t)stream, 0u), (uint32_t)seed,
+                                (uint32_t)(seed >> 32));
+  const float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+  const float u2 = ((float)(w.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
+  const float r = sqrtf(-2.f * logf(u1));
+  float sn, cs;
+  sincospif(2.f * u2, &sn, &cs);
+  if (edge && (ky == 0 || 2 * ky == ny)) return make_float2(r * cs, 0.f);
+  const float h = 0.70710678118654752f;
+  return make_float2(r * cs * h, (edge && 2 * ky > ny) ? -(r * sn * h) : r * sn * h);
+}
+
 // ----------------------------------------------------------------- col_update
 // Two bulk-copy pipelines: innovation lines one item ahead (two stages, or one
 // when shared memory is short) and gain lines one target block ahead (one
@@ -365,6 +393,15 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
           fft_line<NY, V, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
         else                   // the gain wait below synchronises the CTA first
           fft_line<NY, V, false, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
+        if (p.drawn) {   // what += sqrt(ny nx) sqrt(rhat) zhat: the perturbation e_{k,i} in frequency space
+          const double* rh = p.rhat_t + (size_t)i * tab + (size_t)c * NY + t;
+#pragma unroll
+          for (int m = 0; m < V; ++m) {
+            const float a = p.sqrt_G * sqrtf((float)__ldg(rh + T * m));
+            const float2 z = white_spectrum(p.seed, k * p.n_obs + i, t + T * m, c, NY, p.L);
+            wv[i][m] = make_float2(fmaf(a, z.x, wv[i][m].x), fmaf(a, z.y, wv[i][m].y));
+          }
+        }
       } else {
 #pragma unroll
         for (int m = 0; m < V; ++m) wv[i][m] = make_float2(0.f, 0.f);

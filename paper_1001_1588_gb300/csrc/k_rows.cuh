@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   const int nx = p.nx;
   const size_t G = (size_t)p.ny * nx;
   constexpr int es = (ST == kBF16) ? 2 : 4;
-  constexpr int n_in = (MODE == kAnomaly) ? 1 : 2;
+  constexpr int n_in = (MODE == kInnovation) ? 2 : 1;   // u, and e when the perturbations are given
   const uint32_t round_bytes = (uint32_t)LPC * nx * es;
   float2* lines = reinterpret_cast<float2*>(smraw);
   unsigned char* stage = smraw + (((size_t)p.R * pitch * sizeof(float2) + 127) & ~(size_t)127);
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
     const RowTile w = decode_tile(q, p.N, p.n_tiles);
     const size_t row0 = (size_t)w.tile * p.R + (size_t)r * LPC;
     int blk = w.jb;                 // anomaly: block jb; innovation: the jb-th observed block
-    if constexpr (MODE == kInnovation) {
+    if constexpr (MODE != kAnomaly) {
 #pragma unroll
       for (int i = 0; i < kMaxObs; ++i)   // constant indices: the parameter array stays in the constant bank
         if (i == w.jb) blk = p.obs[i];
@@ -114,9 +114,11 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
         const float2 a = load2<ST>(st_row, idx);
         if constexpr (MODE == kAnomaly) {
           v[m] = make_float2(a.x - sv[m].x, a.y - sv[m].y);
-        } else {
+        } else if constexpr (MODE == kInnovation) {
           const float2 ee = load2<ST>(st_row + round_bytes, idx);
           v[m] = make_float2((sv[m].x + ee.x) - a.x, (sv[m].y + ee.y) - a.y);
+        } else {
+          v[m] = make_float2(sv[m].x - a.x, sv[m].y - a.y);
         }
       }
       __syncthreads();   // stage consumed
@@ -305,7 +307,7 @@ inline RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in, bool h
 template <int L, int V, int ST, int MODE>
 cudaError_t row_fwd_LV(RowFwdParams p, int n_fields, cudaStream_t st) {
   constexpr int es = ST == kBF16 ? 2 : 4;
-  RowShape s = row_shape(L, V, p.ny, p.nx, es, MODE == kAnomaly ? 1 : 2, (p.vsel & 2) != 0);
+  RowShape s = row_shape(L, V, p.ny, p.nx, es, MODE == kInnovation ? 2 : 1, (p.vsel & 2) != 0);
   if (s.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   p.R = s.R;
   p.n_tiles = p.ny / s.R;
@@ -369,6 +371,10 @@ cudaError_t row_fwd_L(const RowFwdParams& p, int n_fields, cudaStream_t st) {
   if (p.mode == kAnomaly) {
     if (p.vsel & 1) return row_fwd_LV<L, plan_V(L, 1), ST, kAnomaly>(p, n_fields, st);
     return row_fwd_LV<L, plan_V(L, 0), ST, kAnomaly>(p, n_fields, st);
+  }
+  if (p.mode == kInnovationDrawn) {
+    if (p.vsel & 1) return row_fwd_LV<L, plan_V(L, 1), ST, kInnovationDrawn>(p, n_fields, st);
+    return row_fwd_LV<L, plan_V(L, 0), ST, kInnovationDrawn>(p, n_fields, st);
   }
   if (p.vsel & 1) return row_fwd_LV<L, plan_V(L, 1), ST, kInnovation>(p, n_fields, st);
   return row_fwd_LV<L, plan_V(L, 0), ST, kInnovation>(p, n_fields, st);

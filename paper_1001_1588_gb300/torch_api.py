@@ -86,5 +86,17 @@ class Plan:
                             self.workspace(ensemble.device), _stream_handle(stream))
         return ensemble
 
+    def analyze_seeded(self, ensemble: torch.Tensor, data: torch.Tensor, rhat: torch.Tensor, seed: int,
+                       spectrum: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """In-place analysis with the perturbations drawn by the library from ``seed``; returns ``ensemble``."""
+        self._check(ensemble, (self.M, self.N, self.ny, self.nx), self.dtype, "ensemble")
+        self._check(data, (self.n_obs, self.ny, self.nx), torch.float32, "data")
+        self._check(rhat, (self.n_obs, self.ny, self.nx // 2 + 1), torch.float64, "rhat")
+        if spectrum is not None:
+            self._check(spectrum, (self.spectrum_doubles,), torch.float64, "spectrum")
+        abi.fftenkf_analyze_seeded(self.handle, ensemble, data, rhat, seed, spectrum,
+                                   self.workspace(ensemble.device), _stream_handle(stream))
+        return ensemble
+
     def device_status(self, stream=None) -> int:
         return abi.fftenkf_last_device_status(self.handle, _stream_handle(stream))
