@@ -116,9 +116,10 @@ fftenkf_status fftenkf_analyze(fftenkf_plan plan, void* ensemble, const float* d
  * white N(0, 1) field (Hermitian, real at the self-conjugate wavenumbers), added to the
  * innovation spectrum after its forward transform, so no perturbation field is stored or
  * read.  zhat comes from the counter-based generator Philox4x32-10 (Salmon et al., SC 2011)
- * with counter (k_y', k_x, k n_obs + o, 0) per half-spectrum wavenumber (k_y' = min(k_y,
- * ny - k_y) in the columns k_x = 0 and nx/2), key `seed`, and Box-Muller on the top 24 bits
- * of its first two words; the same seed gives the same analysis.  Other arguments, layouts
+ * with key `seed`: in the columns 0 < k_x < nx/2 the counter (k_y mod ny/2, k_x, k n_obs + o, 0)
+ * serves k_y < ny/2 (words 0, 1) and k_y + ny/2 (words 2, 3); in the columns k_x = 0, nx/2 the
+ * counter is (min(k_y, ny - k_y), k_x, k n_obs + o, 0), words 0, 1; Box-Muller on the top 24
+ * bits of a word pair.  The same seed gives the same analysis.  Other arguments, layouts
  * and errors as fftenkf_analyze. */
 fftenkf_status fftenkf_analyze_seeded(fftenkf_plan plan, void* ensemble, const float* data, const double* rhat,
                                       const double* spectrum, unsigned long long seed, void* workspace,

@@ -11,11 +11,12 @@ in the columns k_x = 0 and k_x = nx/2 the value at k_y > ny/2 is the conjugate o
 ny - k_y, and k_y = 0, ny/2 are real N(0, 1).
 
 The normals come from the counter-based generator Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
-"Parallel random numbers: as easy as 1, 2, 3", SC 2011), counter
-(k_y', k_x, k n_obs + o, 0) with k_y' = min(k_y, ny - k_y) in the columns 0 and nx/2, key
-(seed mod 2^32, seed div 2^32); words 0 and 1 give u_i = (floor(w_i / 2^8) + 1/2) / 2^24 and
-Box-Muller
-n_1 + i n_2 = sqrt(-2 ln u_1) exp(2 pi i u_2).  Complex entries are (n_1 + i n_2) / sqrt(2),
+"Parallel random numbers: as easy as 1, 2, 3", SC 2011), key (seed mod 2^32, seed div 2^32),
+stream s = k n_obs + o.  In the columns 0 < k_x < nx/2 one counter (k_y mod ny/2, k_x, s, 0)
+serves k_y and k_y + ny/2: words (0, 1) for k_y < ny/2, words (2, 3) for the other; in the
+columns k_x = 0, nx/2 the counter is (min(k_y, ny - k_y), k_x, s, 0) with words (0, 1).  A word
+pair (w_a, w_b) gives u = (floor(w / 2^8) + 1/2) / 2^24 and Box-Muller
+n_1 + i n_2 = sqrt(-2 ln u_a) exp(2 pi i u_b).  Complex entries are (n_1 + i n_2) / sqrt(2),
 real ones n_1.  The GPU implements the same definition independently.
 """
 
@@ -53,12 +54,15 @@ def spectral_white(ny: int, nx: int, seed: int, stream: int) -> np.ndarray:
     ky = np.arange(ny)[:, None] * np.ones((1, L + 1), dtype=np.int64)
     kx = np.ones((ny, 1), dtype=np.int64) * np.arange(L + 1)[None, :]
     edge = (kx == 0) | (kx == L)
-    kyc = np.where(edge, np.minimum(ky, (ny - ky) % ny), ky)
+    high = (~edge) & (2 * ky >= ny)                    # interior entries taking words (2, 3)
+    kyc = np.where(edge, np.minimum(ky, (ny - ky) % ny), ky % (ny // 2))
     ctr = np.stack([kyc, kx, np.full_like(ky, stream), np.zeros_like(ky)], axis=-1).astype(np.uint32)
     key = np.broadcast_to(np.array([seed & MASK, (seed >> 32) & MASK], dtype=np.uint32), ctr.shape[:-1] + (2,))
     w = philox4x32_10(ctr, key)
-    u1 = ((w[..., 0] >> np.uint32(8)).astype(np.float64) + 0.5) / 2.0 ** 24
-    u2 = ((w[..., 1] >> np.uint32(8)).astype(np.float64) + 0.5) / 2.0 ** 24
+    wa = np.where(high, w[..., 2], w[..., 0])
+    wb = np.where(high, w[..., 3], w[..., 1])
+    u1 = ((wa >> np.uint32(8)).astype(np.float64) + 0.5) / 2.0 ** 24
+    u2 = ((wb >> np.uint32(8)).astype(np.float64) + 0.5) / 2.0 ** 24
     r = np.sqrt(-2.0 * np.log(u1))
     n1, n2 = r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)
     z = (n1 + 1j * n2) / np.sqrt(2.0)

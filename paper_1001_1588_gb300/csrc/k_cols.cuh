@@ -260,27 +260,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// zhat(k_y, k_x) of one stream: the unitary DFT of a white N(0, 1) field on the half spectrum.
-// Counter (k_y', k_x, stream, 0), k_y' = min(k_y, ny - k_y) in the columns 0 and L so that they
-// are Hermitian in k_y; key = seed.  Words 0, 1 -> u = (w / 2^8 + 1/2) 2^-24 (single precision),
-// Box-Muller n1 + i n2; complex entries (n1 + i n2) / sqrt(2), self-conjugate ones n1.
-__device__ __forceinline__ float2 white_spectrum(unsigned long long seed, int stream, int ky, int kx, int ny, int L) {
-  const bool edge = (kx == 0) || (kx == L);
-  int kyc = ky;
-  if (edge) {
-    const int m = (ny - ky) % ny;
-    kyc = ky < m ? ky : m;
-  }
+// One normal pair from two generator words: u = (w / 2^8 + 1/2) 2^-24 (single precision) and
+// Box-Muller, sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b).
+__device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb) {
+  const float ua = ((float)(wa >> 8) + 0.5f) * 5.9604644775390625e-8f;
+  const float ub = ((float)(wb >> 8) + 0.5f) * 5.9604644775390625e-8f;
+  const float r = sqrtf(-2.f * logf(ua));
+  float sn, cs;
+  sincospif(2.f * ub, &sn, &cs);
+  return make_float2(r * cs, r * sn);
+}
+
+// zhat(k_y, k_x) of one stream in the columns k_x = 0 and L (Hermitian in k_y): counter
+// (min(k_y, ny - k_y), k_x, stream, 0), words 0, 1; real N(0, 1) at the self-conjugate k_y,
+// (n1 + i n2) / sqrt(2) otherwise, conjugated for k_y > ny/2.
+__device__ __forceinline__ float2 white_edge(unsigned long long seed, int stream, int ky, int kx, int ny) {
+  const int m = (ny - ky) % ny;
+  const int kyc = ky < m ? ky : m;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)kyc, (uint32_t)kx, (uint32_t)stream, 0u), (uint32_t)seed,
                                 (uint32_t)(seed >> 32));
-  const float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;
-  const float u2 = ((float)(w.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
-  const float r = sqrtf(-2.f * logf(u1));
-  float sn, cs;
-  sincospif(2.f * u2, &sn, &cs);
-  if (edge && (ky == 0 || 2 * ky == ny)) return make_float2(r * cs, 0.f);
+  const float2 n = box_muller(w.x, w.y);
+  if (ky == 0 || 2 * ky == ny) return make_float2(n.x, 0.f);
   const float h = 0.70710678118654752f;
-  return make_float2(r * cs * h, (edge && 2 * ky > ny) ? -(r * sn * h) : r * sn * h);
+  return make_float2(n.x * h, (2 * ky > ny) ? -(n.y * h) : n.y * h);
 }
 
 // ----------------------------------------------------------------- col_update
@@ -288,7 +290,9 @@ __device__ __forceinline__ float2 white_spectrum(unsigned long long seed, int st
 // when shared memory is short) and gain lines one target block ahead (one
 // stage, read into registers before the next copy is issued).
 // smem: wst [nst][LPC][n_obs][NY] f2 | gst [LPC][n_obs][NY] f2 | xbuf [LPC][PL] f2 | bars[3] | flag
-template <int NY, int V, int NOBS>
+// DRAWN: the perturbations are drawn here (seeded analysis); a separate instantiation, so that the
+// analysis with given perturbations carries none of the generator's code
+template <int NY, int V, int NOBS, bool DRAWN>
 __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kernel(const ColUpdParams p) {
   constexpr int T = NY / V;
   constexpr int PL = col_line_slots(NY);
@@ -393,13 +397,30 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_update_kern
           fft_line<NY, V, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
         else                   // the gain wait below synchronises the CTA first
           fft_line<NY, V, false, false>(wv[i], xbuf, t, p.twY, line_bar<T>(g));
-        if (p.drawn) {   // what += sqrt(ny nx) sqrt(rhat) zhat: the perturbation e_{k,i} in frequency space
+        if constexpr (DRAWN) {   // what += sqrt(ny nx) sqrt(rhat) zhat: the perturbation e_{k,i} in frequency space
           const double* rh = p.rhat_t + (size_t)i * tab + (size_t)c * NY + t;
+          const int stream = k * p.n_obs + i;
+          if (c != 0 && c != p.L) {
+            // interior column: one generator call per k_y < ny/2 serves k_y (words 0, 1) and
+            // k_y + ny/2 (words 2, 3), the slots m and m + V/2 of this thread
+            const float h = 0.70710678118654752f;
 #pragma unroll
-          for (int m = 0; m < V; ++m) {
-            const float a = p.sqrt_G * sqrtf((float)__ldg(rh + T * m));
-            const float2 z = white_spectrum(p.seed, k * p.n_obs + i, t + T * m, c, NY, p.L);
-            wv[i][m] = make_float2(fmaf(a, z.x, wv[i][m].x), fmaf(a, z.y, wv[i][m].y));
+            for (int m = 0; m < V / 2; ++m) {
+              const uint4 w4 = philox4x32_10(make_uint4((uint32_t)(t + T * m), (uint32_t)c, (uint32_t)stream, 0u),
+                                             (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+              const float2 zl = box_muller(w4.x, w4.y), zh = box_muller(w4.z, w4.w);
+              const float al = h * p.sqrt_G * sqrtf((float)__ldg(rh + T * m));
+              const float ah = h * p.sqrt_G * sqrtf((float)__ldg(rh + T * (m + V / 2)));
+              wv[i][m] = make_float2(fmaf(al, zl.x, wv[i][m].x), fmaf(al, zl.y, wv[i][m].y));
+              wv[i][m + V / 2] = make_float2(fmaf(ah, zh.x, wv[i][m + V / 2].x), fmaf(ah, zh.y, wv[i][m + V / 2].y));
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+              const float a = p.sqrt_G * sqrtf((float)__ldg(rh + T * m));
+              const float2 z = white_edge(p.seed, stream, t + T * m, c, NY);
+              wv[i][m] = make_float2(fmaf(a, z.x, wv[i][m].x), fmaf(a, z.y, wv[i][m].y));
+            }
           }
         }
       } else {
@@ -502,7 +523,7 @@ inline cudaError_t col_update_NYV(const ColUpdParams& p, cudaStream_t st) {
   if (smem == 0) return cudaErrorInvalidConfiguration;
   ColUpdParams q = p;
   q.n_stages = nst;
-  auto kern = col_update_kernel<NY, V, NOBS>;
+  auto kern = p.drawn ? col_update_kernel<NY, V, NOBS, true> : col_update_kernel<NY, V, NOBS, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
