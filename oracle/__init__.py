@@ -13,6 +13,8 @@ Modules
          eq. (spectral-enkf) / (spectral-multi-enkf) update
   dense  brute-force forms used to pin the above on tiny grids: sample covariance
          C_N, diag(F C_N F*), and the dense EnKF update eq. (enkf) / (multi-enkf)
+  sine   the real sine transform variant (Sec. 4): orthonormal DST-I on the interior nodes,
+         boundary nodes unchanged
   mlp    FP64 forward/backward of the spectral-variance denoiser and its
          radial binning (not in the paper; parity of trained weights unpinned)
 
