@@ -257,6 +257,41 @@ fftenkf_status fftenkf_mlp_adam(float* params, float* m, float* v, const float* 
 fftenkf_status fftenkf_denoise_spectrum(fftenkf_denoiser d, const float* params, const double* chat_in,
                                         double* chat_out, int n_members, int* used_fallback, void* stream);
 
+/* ---------------------------------------------------------------- real sine transform
+ * The variant of Sec. 4: the real sine FFT in place of the periodic DFT, which leaves the
+ * boundary unchanged.  The grid ny x nx includes its boundary nodes (first and last row and
+ * column); the (ny-2) x (nx-2) interior is transformed by the orthonormal type-I sine transform
+ * S_m[k][j] = sqrt(2/(m+1)) sin(pi (k+1)(j+1)/(m+1)) in each direction, and eq. (dii) and
+ * eq. (spectral-multi-enkf) are applied with S in place of F (real coefficients; observed
+ * blocks' mutual cross-covariances neglected as for the periodic plan; gain 0 where
+ * chat + rhat == 0).  Boundary nodes of the ensemble are left as they are.
+ * The transform is computed exactly as the periodic one of the odd extension of the interior to
+ * the period 2(ny-1) x 2(nx-1), whose DFT is -S of the interior at the wavenumbers 1..m of each
+ * axis (and their negatives) and zero on the lines 0 and m+1: the plan extends the inputs into
+ * plan-owned buffers, runs the periodic analysis there and copies the interior back.  So
+ * 2(ny-1) and 2(nx-1) must satisfy the periodic plan's rules (ny-1 in {2^a, 3*2^a} up to 2048,
+ * nx-1 in {2^a, 3*2^a} up to 4096, both at least 8), else EUNSUPPORTED; the plan allocates
+ * about 4x the ensemble, perturbations and data, and 4x the work of a periodic analysis on
+ * ny x nx.  Device pointers need only the alignment of their element type.
+ *   ensemble      [M][N][ny][nx] storage dtype, in place
+ *   data          [n_obs][ny][nx] float; perturbations [N][n_obs][ny][nx] storage dtype
+ *                 (only their interior nodes enter)
+ *   rhat          [n_obs][ny-2][nx-2] double: data-error variance per sine wavenumber
+ *                 (R = r I on the interior gives rhat = r)
+ *   spectrum_out  fftenkf_sine_spectrum_size doubles: n_obs auto tables chat^(oo) followed by
+ *                 n_obs * n_unobserved cross tables chat^(jo) (observed o ascending, then
+ *                 unobserved j ascending), each [ny-2][nx-2] real. */
+typedef struct fftenkf_sine_plan_s* fftenkf_sine_plan;
+fftenkf_status fftenkf_sine_plan_create(fftenkf_sine_plan* plan, const fftenkf_dims* dims,
+                                        const uint8_t* observed_mask);
+fftenkf_status fftenkf_sine_plan_destroy(fftenkf_sine_plan plan);
+fftenkf_status fftenkf_sine_spectrum_size(fftenkf_sine_plan plan, size_t* n_doubles);
+fftenkf_status fftenkf_sine_estimate_spectrum(fftenkf_sine_plan plan, const void* ensemble, double* spectrum_out,
+                                              void* stream);
+fftenkf_status fftenkf_sine_analyze(fftenkf_sine_plan plan, void* ensemble, const float* data,
+                                    const void* perturbations, const double* rhat, void* stream);
+fftenkf_status fftenkf_sine_last_device_status(fftenkf_sine_plan plan, void* stream);
+
 /* Static description of a status code. */
 const char* fftenkf_status_string(fftenkf_status s);
 /* Message of the last failing call on this host thread ("" if none). */

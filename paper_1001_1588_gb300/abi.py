@@ -77,6 +77,13 @@ _SIGNATURES = [
                                         ctypes.c_float, ctypes.c_void_p]),
     ("fftenkf_denoise_spectrum", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    ("fftenkf_sine_plan_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fftenkf_dims),
+                                                ctypes.c_char_p]),
+    ("fftenkf_sine_plan_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("fftenkf_sine_spectrum_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("fftenkf_sine_estimate_spectrum", ctypes.c_int, [ctypes.c_void_p] * 4),
+    ("fftenkf_sine_analyze", ctypes.c_int, [ctypes.c_void_p] * 6),
+    ("fftenkf_sine_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("fftenkf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_last_error", ctypes.c_char_p, []),
 ]
@@ -167,6 +174,38 @@ def fftenkf_estimate_spectrum_static(ensemble, ny, nx, n_members, storage, spect
     """Allocation-free single-block estimate (scratch in the library's static device array)."""
     check(lib().fftenkf_estimate_spectrum_static(_p(ensemble), ny, nx, n_members, storage, _p(spectrum_out), stream),
           "fftenkf_estimate_spectrum_static")
+
+
+def fftenkf_sine_plan_create(ny, nx, n_blocks, n_members, storage, observed_mask):
+    d = fftenkf_dims(ny, nx, n_blocks, n_members, storage)
+    plan = ctypes.c_void_p()
+    mask = bytes(int(bool(m)) for m in observed_mask)
+    check(lib().fftenkf_sine_plan_create(ctypes.byref(plan), ctypes.byref(d), mask), "fftenkf_sine_plan_create")
+    return plan.value
+
+
+def fftenkf_sine_plan_destroy(plan):
+    check(lib().fftenkf_sine_plan_destroy(plan), "fftenkf_sine_plan_destroy")
+
+
+def fftenkf_sine_spectrum_size(plan) -> int:
+    n = ctypes.c_size_t()
+    check(lib().fftenkf_sine_spectrum_size(plan, ctypes.byref(n)), "fftenkf_sine_spectrum_size")
+    return n.value
+
+
+def fftenkf_sine_estimate_spectrum(plan, ensemble, spectrum_out, stream=None):
+    check(lib().fftenkf_sine_estimate_spectrum(plan, _p(ensemble), _p(spectrum_out), stream),
+          "fftenkf_sine_estimate_spectrum")
+
+
+def fftenkf_sine_analyze(plan, ensemble, data, perturbations, rhat, stream=None):
+    check(lib().fftenkf_sine_analyze(plan, _p(ensemble), _p(data), _p(perturbations), _p(rhat), stream),
+          "fftenkf_sine_analyze")
+
+
+def fftenkf_sine_last_device_status(plan, stream=None) -> int:
+    return lib().fftenkf_sine_last_device_status(plan, stream)
 
 
 def fftenkf_last_device_status(plan, stream=None) -> int:

@@ -100,3 +100,53 @@ class Plan:
 
     def device_status(self, stream=None) -> int:
         return abi.fftenkf_last_device_status(self.handle, _stream_handle(stream))
+
+
+class SinePlan:
+    """The real sine transform variant (Sec. 4): grid ny x nx including its boundary nodes, which
+    the analysis leaves unchanged; the interior is analysed in the orthonormal DST-I basis."""
+
+    def __init__(self, ny: int, nx: int, n_blocks: int, n_members: int, storage: torch.dtype,
+                 observed: Sequence[int]):
+        if storage not in _STORAGE:
+            raise TypeError("storage must be torch.float32 or torch.bfloat16")
+        self.ny, self.nx, self.M, self.N = ny, nx, n_blocks, n_members
+        self.dtype = storage
+        self.observed = [int(bool(o)) for o in observed]
+        self.n_obs = sum(self.observed)
+        self.handle = abi.fftenkf_sine_plan_create(ny, nx, n_blocks, n_members, _STORAGE[storage], self.observed)
+        self.spectrum_doubles = abi.fftenkf_sine_spectrum_size(self.handle)
+
+    def close(self):
+        if self.handle:
+            abi.fftenkf_sine_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    _check = Plan._check
+
+    def estimate_spectrum(self, ensemble: torch.Tensor, out: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+        self._check(ensemble, (self.M, self.N, self.ny, self.nx), self.dtype, "ensemble")
+        if out is None:
+            out = torch.empty(self.spectrum_doubles, dtype=torch.float64, device=ensemble.device)
+        abi.fftenkf_sine_estimate_spectrum(self.handle, ensemble, out, _stream_handle(stream))
+        return out
+
+    def analyze(self, ensemble: torch.Tensor, data: torch.Tensor, perturbations: torch.Tensor,
+                rhat: torch.Tensor, stream=None) -> torch.Tensor:
+        """In-place analysis of ``ensemble``; rhat [n_obs][ny-2][nx-2] per sine wavenumber."""
+        self._check(ensemble, (self.M, self.N, self.ny, self.nx), self.dtype, "ensemble")
+        self._check(data, (self.n_obs, self.ny, self.nx), torch.float32, "data")
+        self._check(perturbations, (self.N, self.n_obs, self.ny, self.nx), self.dtype, "perturbations")
+        self._check(rhat, (self.n_obs, self.ny - 2, self.nx - 2), torch.float64, "rhat")
+        abi.fftenkf_sine_analyze(self.handle, ensemble, data, perturbations, rhat, _stream_handle(stream))
+        return ensemble
+
+    def device_status(self, stream=None) -> int:
+        return abi.fftenkf_sine_last_device_status(self.handle, _stream_handle(stream))
