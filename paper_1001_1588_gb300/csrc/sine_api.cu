@@ -33,63 +33,89 @@ fftenkf_status sfail(fftenkf_status s, const std::string& msg) {
   return s;
 }
 
-// source index (1..n-2) and sign of extension coordinate e in [0, 2(n-1)); 0 for a zero node
-__device__ __forceinline__ int odd_source(int e, int n, int* neg) {
-  const int P = 2 * (n - 1);
-  if (e == 0 || e == n - 1) return 0;
-  if (e < n - 1) {
-    *neg = 0;
-    return e;
-  }
-  *neg = 1;
-  return P - e;
-}
+constexpr int kMaxRow = 4104;   // words of one source row in shared memory (nx <= 4097)
 
-template <typename W>
-__device__ __forceinline__ W odd_word(const W* row, int x, int nx, int neg_row, bool zero_row) {
-  int neg = 0;
-  const int sx = odd_source(x, nx, &neg);
-  if (zero_row || sx == 0) return W(0);
-  const W v = row[sx];
-  const W sign = W(W(1) << (8 * sizeof(W) - 1));   // IEEE sign bit of float / bfloat16
-  return (neg ^ neg_row) ? W(v ^ sign) : v;
-}
-
-// dst [F][Py][Px] = odd extension of the interior of src [F][ny][nx]; two words per thread
+// dst [F][Py][Px] = odd extension of the interior of src [F][ny][nx].  One unit per source row:
+// interior row sy is staged in shared memory once and written to the extension rows sy and
+// Py - sy (negated), 16 bytes per store; unit sy = 0 writes the two zero rows 0 and ny - 1.
 template <typename W>
 __global__ void __launch_bounds__(kThreads) odd_extend_kernel(const W* __restrict__ src, W* __restrict__ dst,
                                                               int F, int ny, int nx) {
+  constexpr int VEC = 16 / sizeof(W);
+  const W sign = W(W(1) << (8 * sizeof(W) - 1));   // IEEE sign bit of float / bfloat16
+  __shared__ W row[kMaxRow];
   const int Py = 2 * (ny - 1), Px = 2 * (nx - 1);
-  const long long rows = (long long)F * Py;
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int f = (int)(r / Py), y = (int)(r % Py);
-    int neg_row = 0;
-    const int sy = odd_source(y, ny, &neg_row);
-    const W* srow = src + ((size_t)f * ny + sy) * nx;
-    W* drow = dst + (size_t)r * Px;
-    for (int x = 2 * threadIdx.x; x < Px; x += 2 * kThreads) {
-      const W a = odd_word(srow, x, nx, neg_row, sy == 0);
-      const W b = odd_word(srow, x + 1, nx, neg_row, sy == 0);
-      if constexpr (sizeof(W) == 2) {
-        reinterpret_cast<uint32_t*>(drow)[x >> 1] = uint32_t(a) | (uint32_t(b) << 16);
-      } else {
-        reinterpret_cast<uint2*>(drow)[x >> 1] = make_uint2(a, b);
+  const long long units = (long long)F * (ny - 1);
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int f = (int)(u / (ny - 1)), sy = (int)(u % (ny - 1));
+    W* d0 = dst + ((size_t)f * Py + (sy == 0 ? 0 : sy)) * Px;
+    W* d1 = dst + ((size_t)f * Py + (sy == 0 ? ny - 1 : Py - sy)) * Px;
+    if (sy == 0) {
+      for (int v = threadIdx.x; v < Px / VEC; v += kThreads) {
+        reinterpret_cast<uint4*>(d0)[v] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(d1)[v] = make_uint4(0, 0, 0, 0);
       }
+      continue;
+    }
+    const W* s = src + ((size_t)f * ny + sy) * nx;
+    __syncthreads();   // the previous unit's readers are done with row[]
+    for (int x = threadIdx.x; x < nx; x += kThreads) row[x] = s[x];
+    __syncthreads();
+    for (int v = threadIdx.x; v < Px / VEC; v += kThreads) {
+      alignas(16) W a[VEC];
+      alignas(16) W b[VEC];
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) {
+        const int x = v * VEC + i;
+        W w = 0, n = 0;
+        if (x >= 1 && x <= nx - 2) {
+          w = row[x];
+          n = W(w ^ sign);
+        } else if (x >= nx) {
+          n = row[Px - x];
+          w = W(n ^ sign);
+        }
+        a[i] = w;
+        b[i] = n;
+      }
+      reinterpret_cast<uint4*>(d0)[v] = *reinterpret_cast<const uint4*>(a);
+      reinterpret_cast<uint4*>(d1)[v] = *reinterpret_cast<const uint4*>(b);
     }
   }
 }
 
-// interior of dst [F][ny][nx] = the same nodes of ext [F][Py][Px]; boundary nodes untouched
+// interior of dst [F][ny][nx] = the same nodes of ext [F][Py][Px]; boundary nodes untouched.
+// One row per unit: the extension row (16-byte aligned) is staged in shared memory with 16-byte
+// loads, and the user row, whose start has any element alignment, is written as a scalar head up
+// to the first 16-byte boundary, 16-byte chunks, and a scalar tail.
 template <typename W>
 __global__ void __launch_bounds__(kThreads) interior_copy_kernel(const W* __restrict__ ext, W* __restrict__ dst,
                                                                  int F, int ny, int nx) {
+  constexpr int VEC = 16 / sizeof(W);
+  __shared__ __align__(16) W row[kMaxRow];
   const int Px = 2 * (nx - 1), Py = 2 * (ny - 1);
+  const int nvec = (nx + VEC - 1) / VEC;   // vectors covering nodes [0, nx) of the row; nvec * VEC <= Px
+  const int n = nx - 2;
   const long long rows = (long long)F * (ny - 2);
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int f = (int)(r / (ny - 2)), y = 1 + (int)(r % (ny - 2));
-    const W* erow = ext + ((size_t)f * Py + y) * Px;
-    W* drow = dst + ((size_t)f * ny + y) * nx;
-    for (int x = 1 + threadIdx.x; x < nx - 1; x += kThreads) drow[x] = erow[x];
+    const uint4* erow = reinterpret_cast<const uint4*>(ext + ((size_t)f * Py + y) * Px);
+    __syncthreads();   // the previous row's readers are done with row[]
+    for (int v = threadIdx.x; v < nvec; v += kThreads) reinterpret_cast<uint4*>(row)[v] = erow[v];
+    __syncthreads();
+    W* d = dst + ((size_t)f * ny + y) * nx + 1;
+    const int mis = (int)(reinterpret_cast<uintptr_t>(d) % 16) / (int)sizeof(W);
+    int head = (VEC - mis) % VEC;
+    if (head > n) head = n;
+    if ((int)threadIdx.x < head) d[threadIdx.x] = row[1 + threadIdx.x];
+    const int chunks = (n - head) / VEC;
+    for (int c = threadIdx.x; c < chunks; c += kThreads) {
+      alignas(16) W t[VEC];
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) t[i] = row[1 + head + c * VEC + i];
+      reinterpret_cast<uint4*>(d + head)[c] = *reinterpret_cast<const uint4*>(t);
+    }
+    for (int x = head + chunks * VEC + threadIdx.x; x < n; x += kThreads) d[x] = row[1 + x];
   }
 }
 
@@ -99,16 +125,14 @@ __global__ void __launch_bounds__(kThreads) interior_copy_kernel(const W* __rest
 __global__ void __launch_bounds__(kThreads) rhat_extend_kernel(const double* __restrict__ r, double* __restrict__ out,
                                                                int n_obs, int ny, int nx) {
   const int Py = 2 * (ny - 1);
-  const long long n = (long long)n_obs * Py * nx;
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
-    const int kx = (int)(i % nx);
-    const int ky = (int)((i / nx) % Py);
-    const int o = (int)(i / ((long long)nx * Py));
+  for (int row = blockIdx.x; row < n_obs * Py; row += gridDim.x) {
+    const int o = row / Py, ky = row % Py;
     const int a = ky < Py - ky ? ky : Py - ky;
-    double v = 1.0;
-    if (a >= 1 && a <= ny - 2 && kx >= 1 && kx <= nx - 2)
-      v = r[((size_t)o * (ny - 2) + (a - 1)) * (nx - 2) + (kx - 1)];
-    out[i] = v;
+    const bool inside = a >= 1 && a <= ny - 2;
+    const double* src = r + ((size_t)o * (ny - 2) + (inside ? a - 1 : 0)) * (nx - 2);
+    double* dst = out + (size_t)row * nx;
+    for (int kx = threadIdx.x; kx < nx; kx += kThreads)
+      dst[kx] = (inside && kx >= 1 && kx <= nx - 2) ? src[kx - 1] : 1.0;
   }
 }
 
@@ -159,7 +183,7 @@ static void release(fftenkf_sine_plan_s* p) {
 static bool aligned_to(const void* q, size_t a) { return (reinterpret_cast<uintptr_t>(q) % a) == 0; }
 
 static cudaError_t extend(const void* src, void* dst, int F, int ny, int nx, size_t elem, cudaStream_t s) {
-  const long long rows = (long long)F * 2 * (ny - 1);
+  const long long rows = (long long)F * (ny - 1);
   if (elem == 2)
     odd_extend_kernel<uint16_t><<<grid_for(rows), kThreads, 0, s>>>(static_cast<const uint16_t*>(src),
                                                                    static_cast<uint16_t*>(dst), F, ny, nx);
@@ -176,6 +200,7 @@ extern "C" fftenkf_status fftenkf_sine_plan_create(fftenkf_sine_plan* plan, cons
   const fftenkf_dims d = *dims;
   if (d.ny < 3 || d.nx < 3) return sfail(FFTENKF_EINVAL, "the grid needs interior nodes (ny, nx >= 3)");
   if (d.ny - 1 > 2048 || d.nx - 1 > 4096) return sfail(FFTENKF_EUNSUPPORTED, "ny - 1 <= 2048 and nx - 1 <= 4096");
+  if ((2 * (d.nx - 1)) % 8 != 0) return sfail(FFTENKF_EUNSUPPORTED, "nx - 1 must be 2^a or 3*2^a, at least 8");
   fftenkf_dims e = d;
   e.ny = 2 * (d.ny - 1);
   e.nx = 2 * (d.nx - 1);
@@ -267,9 +292,8 @@ extern "C" fftenkf_status fftenkf_sine_analyze(fftenkf_sine_plan p, void* ensemb
   if (ce == cudaSuccess) ce = extend(data, p->ext_data, p->n_obs, p->ny, p->nx, 4, s);
   if (ce == cudaSuccess) ce = extend(perturbations, p->ext_pert, p->N * p->n_obs, p->ny, p->nx, p->elem, s);
   if (ce == cudaSuccess) {
-    const long long n = (long long)p->n_obs * p->Py * (p->Px / 2 + 1);
-    rhat_extend_kernel<<<grid_for((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(rhat, p->ext_rhat, p->n_obs,
-                                                                                   p->ny, p->nx);
+    rhat_extend_kernel<<<grid_for((long long)p->n_obs * p->Py), kThreads, 0, s>>>(rhat, p->ext_rhat, p->n_obs,
+                                                                                 p->ny, p->nx);
     ce = cudaGetLastError();
   }
   if (ce != cudaSuccess) return sfail(FFTENKF_ECUDA, std::string("sine extend: ") + cudaGetErrorString(ce));

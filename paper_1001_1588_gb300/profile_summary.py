@@ -25,7 +25,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # kernels of one analysis with the library's estimated spectrum, in launch order
 PASS_ORDER = ["rhat_transpose", "mean", "row_fwd_anomaly", "col_stats", "row_fwd_innovation", "col_update", "row_inv"]
 OURS = re.compile(r"(rhat_transpose|mean_kernel|mean_staged_kernel|row_fwd_kernel|col_stats_kernel|gain_kernel|"
-                  r"coupled_gain_kernel|col_update_kernel|row_inv_kernel|chat_out)")
+                  r"coupled_gain_kernel|col_update_kernel|row_inv_kernel|chat_out|odd_extend_kernel|interior_copy_kernel|"
+                  r"rhat_extend_kernel|sine_tables_kernel)")
 
 
 def read(path):
