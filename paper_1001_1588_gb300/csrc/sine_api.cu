@@ -85,37 +85,52 @@ __global__ void __launch_bounds__(kThreads) odd_extend_kernel(const W* __restric
 }
 
 // interior of dst [F][ny][nx] = the same nodes of ext [F][Py][Px]; boundary nodes untouched.
-// One row per unit: the extension row (16-byte aligned) is staged in shared memory with 16-byte
-// loads, and the user row, whose start has any element alignment, is written as a scalar head up
-// to the first 16-byte boundary, 16-byte chunks, and a scalar tail.
+// R rows per unit (32 KB of shared memory): the extension rows (16-byte aligned) are staged with
+// 16-byte loads, all R in flight before one barrier, and each user row, whose start has any element
+// alignment, is written as a scalar head up to the first 16-byte boundary, 16-byte chunks, and a
+// scalar tail.
 template <typename W>
 __global__ void __launch_bounds__(kThreads) interior_copy_kernel(const W* __restrict__ ext, W* __restrict__ dst,
                                                                  int F, int ny, int nx) {
   constexpr int VEC = 16 / sizeof(W);
-  __shared__ __align__(16) W row[kMaxRow];
+  constexpr int R = 8 / sizeof(W);   // 4 BF16 rows or 2 FP32 rows
+  __shared__ __align__(16) W row[R][kMaxRow];
   const int Px = 2 * (nx - 1), Py = 2 * (ny - 1);
   const int nvec = (nx + VEC - 1) / VEC;   // vectors covering nodes [0, nx) of the row; nvec * VEC <= Px
   const int n = nx - 2;
   const long long rows = (long long)F * (ny - 2);
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int f = (int)(r / (ny - 2)), y = 1 + (int)(r % (ny - 2));
-    const uint4* erow = reinterpret_cast<const uint4*>(ext + ((size_t)f * Py + y) * Px);
-    __syncthreads();   // the previous row's readers are done with row[]
-    for (int v = threadIdx.x; v < nvec; v += kThreads) reinterpret_cast<uint4*>(row)[v] = erow[v];
-    __syncthreads();
-    W* d = dst + ((size_t)f * ny + y) * nx + 1;
-    const int mis = (int)(reinterpret_cast<uintptr_t>(d) % 16) / (int)sizeof(W);
-    int head = (VEC - mis) % VEC;
-    if (head > n) head = n;
-    if ((int)threadIdx.x < head) d[threadIdx.x] = row[1 + threadIdx.x];
-    const int chunks = (n - head) / VEC;
-    for (int c = threadIdx.x; c < chunks; c += kThreads) {
-      alignas(16) W t[VEC];
-#pragma unroll
-      for (int i = 0; i < VEC; ++i) t[i] = row[1 + head + c * VEC + i];
-      reinterpret_cast<uint4*>(d + head)[c] = *reinterpret_cast<const uint4*>(t);
+  const long long units = (rows + R - 1) / R;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    __syncthreads();   // the previous unit's readers are done with row[][]
+    for (int i = threadIdx.x; i < R * nvec; i += kThreads) {
+      const int rr = i / nvec, v = i - rr * nvec;
+      const long long r = u * R + rr;
+      if (r < rows) {
+        const int f = (int)(r / (ny - 2)), y = 1 + (int)(r % (ny - 2));
+        reinterpret_cast<uint4*>(row[rr])[v] =
+            reinterpret_cast<const uint4*>(ext + ((size_t)f * Py + y) * Px)[v];
+      }
     }
-    for (int x = head + chunks * VEC + threadIdx.x; x < n; x += kThreads) d[x] = row[1 + x];
+    __syncthreads();
+    for (int rr = 0; rr < R; ++rr) {
+      const long long r = u * R + rr;
+      if (r >= rows) break;
+      const int f = (int)(r / (ny - 2)), y = 1 + (int)(r % (ny - 2));
+      const W* sr = row[rr];
+      W* d = dst + ((size_t)f * ny + y) * nx + 1;
+      const int mis = (int)(reinterpret_cast<uintptr_t>(d) % 16) / (int)sizeof(W);
+      int head = (VEC - mis) % VEC;
+      if (head > n) head = n;
+      if ((int)threadIdx.x < head) d[threadIdx.x] = sr[1 + threadIdx.x];
+      const int chunks = (n - head) / VEC;
+      for (int c = threadIdx.x; c < chunks; c += kThreads) {
+        alignas(16) W t[VEC];
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) t[i] = sr[1 + head + c * VEC + i];
+        reinterpret_cast<uint4*>(d + head)[c] = *reinterpret_cast<const uint4*>(t);
+      }
+      for (int x = head + chunks * VEC + threadIdx.x; x < n; x += kThreads) d[x] = sr[1 + x];
+    }
   }
 }
 
@@ -302,11 +317,11 @@ extern "C" fftenkf_status fftenkf_sine_analyze(fftenkf_sine_plan p, void* ensemb
   if (st != FFTENKF_OK) return st;
   const long long rows = (long long)p->M * p->N * (p->ny - 2);
   if (p->elem == 2)
-    interior_copy_kernel<uint16_t><<<grid_for(rows), kThreads, 0, s>>>(static_cast<const uint16_t*>(p->ext_ens),
+    interior_copy_kernel<uint16_t><<<grid_for((rows + 3) / 4), kThreads, 0, s>>>(static_cast<const uint16_t*>(p->ext_ens),
                                                                       static_cast<uint16_t*>(ensemble), p->M * p->N,
                                                                       p->ny, p->nx);
   else
-    interior_copy_kernel<uint32_t><<<grid_for(rows), kThreads, 0, s>>>(static_cast<const uint32_t*>(p->ext_ens),
+    interior_copy_kernel<uint32_t><<<grid_for((rows + 1) / 2), kThreads, 0, s>>>(static_cast<const uint32_t*>(p->ext_ens),
                                                                       static_cast<uint32_t*>(ensemble), p->M * p->N,
                                                                       p->ny, p->nx);
   ce = cudaGetLastError();
