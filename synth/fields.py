@@ -292,3 +292,28 @@ def make_batched_items(count: int = 256, seed: int = 20260004, sides: Sequence[i
         p.meta.update(it)
         out.append(p)
     return out
+
+
+def smooth_mappings(seed: int, K: int, ny: int, nx: int, amp: float, ell: float) -> np.ndarray:
+    """K random smooth displacement fields T_k = (T_x, T_y), float32 [2][K][ny][nx], in grid units
+    (Sec. 2.2: random smooth mappings from Fourier series whose coefficients decay quickly; here a
+    squared-exponential spectrum of length ell cells), each component scaled to max |T| = amp."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S = se_spectrum(ny, nx, ell)
+    T = np.empty((2, K, ny, nx), dtype=np.float32)
+    for c in range(2):
+        for k in range(K):
+            g = gaussian_field(S, rng.standard_normal((ny, nx)))
+            T[c, k] = (amp * g / max(np.abs(g).max(), 1e-30)).astype(np.float32)
+    return T
+
+
+def smooth_members(seed: int, M: int, K: int, ny: int, nx: int, ell: float) -> np.ndarray:
+    """M x K unit-variance squared-exponential fields, float32 [M][K][ny][nx]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S = se_spectrum(ny, nx, ell)
+    u = np.empty((M, K, ny, nx), dtype=np.float32)
+    for j in range(M):
+        for k in range(K):
+            u[j, k] = gaussian_field(S, rng.standard_normal((ny, nx))).astype(np.float32)
+    return u
