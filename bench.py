@@ -54,10 +54,11 @@ def parse():
     ap.add_argument("--no-seeded", action="store_true", help="skip the timing of the seeded (drawn-perturbation) analysis")
     ap.add_argument("--no-side", action="store_true",
                     help="sine workload: skip the side timing of the periodic extension-size analysis")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "coupled", "sine"],
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "coupled", "sine", "morph"],
                     help="large: 4 blocks 4096^2 N=20 (default, the headline); batched: 256 mixed analyses; "
                          "coupled: 3 blocks 4096^2 N=20 with coupled observed blocks; "
-                         "sine: real sine transform variant on 2049^2 nodes, 4 blocks, N=20")
+                         "sine: real sine transform variant on 2049^2 nodes, 4 blocks, N=20; "
+                         "morph: morphing FFT EnKF, 2 blocks 4096^2 N=20 FP32 (T_x, T_y, r^(1) observed)")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
@@ -710,6 +711,113 @@ def run_batched(a):
     return 0
 
 
+def morph_bytes(ny, nx, M_, K):
+    """Algorithmic bytes of the morphing kernels (FP32): forward reads T (8 B) and M members and
+    writes M residuals per (member, node), plus the reference once; the inverse reads T and M
+    residuals and writes M members per (member, node), plus the reference once; the reference mean
+    reads C = M+2 channels of K members and writes C planes."""
+    plane = ny * nx
+    fwd = K * plane * (8 + 8 * M_) + 4 * M_ * plane
+    inv = K * plane * (8 + 8 * M_) + 4 * M_ * plane
+    ref = 4 * (M_ + 2) * plane * (K + 1)
+    return fwd, ref, inv
+
+
+def run_morph(a):
+    """Morphing FFT EnKF (Sec. 2.2) at 4096^2, M = 2 physical blocks, N = 20, FP32: transform of the
+    members and the data, FFT EnKF on the extended state (T_x, T_y, r^(1) observed, r^(2)
+    unobserved), reference mean, inverse transform of the members and of the reference.  Inputs:
+    smooth seeded fields (a 128^2 seeded grid upsampled on the device), displacements of up to 3
+    cells, data perturbations of standard deviation 0.1, rhat = 0.01."""
+    import torch
+    from paper_1001_1588_gb300 import abi, torch_api
+    from synth import fields
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    ny, nx, K, M_, n_iter = a.ny, a.nx, a.members, 2, 20
+    up = torch.nn.Upsample(size=(ny, nx), mode="bilinear", align_corners=False)
+
+    def smooth(arr):
+        return up(torch.from_numpy(arr).to(dev)).contiguous()
+
+    u = smooth(fields.smooth_members(61, M_, K, 128, 128, ell=6.0))
+    T = smooth(fields.smooth_mappings(62, K, 128, 128, amp=3.0, ell=6.0))
+    u_ref = smooth(fields.smooth_members(63, M_, 1, 128, 128, ell=6.0))[:, 0].contiguous()
+    d = smooth(fields.smooth_members(64, 1, 1, 128, 128, ell=6.0))
+    T0 = smooth(fields.smooth_mappings(65, 1, 128, 128, amp=3.0, ell=6.0))
+    g = torch.Generator(device=dev).manual_seed(66)
+    pert = (0.1 * torch.randn((K, 3, ny, nx), generator=g, device=dev)).contiguous()
+    rhat = torch.full((3, ny, nx // 2 + 1), 0.01, dtype=torch.float64, device=dev)
+    ext = torch.empty((M_ + 2, K, ny, nx), dtype=torch.float32, device=dev)
+    data = torch.empty((3, 1, ny, nx), dtype=torch.float32, device=dev)
+    ext_ref = torch.empty((M_ + 2, ny, nx), dtype=torch.float32, device=dev)
+    ua = torch.empty((M_, K, ny, nx), dtype=torch.float32, device=dev)
+    ua_ref = torch.empty((M_, 1, ny, nx), dtype=torch.float32, device=dev)
+    plan = torch_api.Plan(ny, nx, M_ + 2, K, torch.float32, (1, 1, 1, 0))
+    s = torch.cuda.current_stream(dev).cuda_stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    acc = [0.0] * 5
+
+    def step(timed):
+        ext[:2].copy_(T)
+        data[:2].copy_(T0)
+        if timed:
+            ev[0].record()
+        abi.fftenkf_morph_forward(u, u_ref, ext, M_, K, ny, nx, n_iter, s)
+        abi.fftenkf_morph_forward(d, u_ref, data, 1, 1, ny, nx, n_iter, s)
+        if timed:
+            ev[1].record()
+        plan.analyze(ext, data.view(3, ny, nx), pert, rhat)
+        if timed:
+            ev[2].record()
+        abi.fftenkf_morph_reference(ext, ext_ref, M_ + 2, K, ny, nx, s)
+        if timed:
+            ev[3].record()
+        abi.fftenkf_morph_inverse(ext, u_ref, ua, M_, K, ny, nx, s)
+        abi.fftenkf_morph_inverse(ext_ref, u_ref, ua_ref, M_, 1, ny, nx, s)
+        if timed:
+            ev[4].record()
+            torch.cuda.synchronize(dev)
+            for i in range(4):
+                acc[i] += ev[i].elapsed_time(ev[i + 1])
+            acc[4] += ev[0].elapsed_time(ev[4])
+
+    for _ in range(max(a.warmup, 1)):
+        step(False)
+    torch.cuda.synchronize(dev)
+    if plan.device_status() != 0:
+        raise RuntimeError("device status: %s" % abi.fftenkf_last_error())
+    with ClockSampler(None) as clk:
+        clk.begin()
+        for _ in range(a.steps):
+            step(True)
+    plan.close()
+    f_ms, an_ms, r_ms, i_ms, ms = (x / a.steps for x in acc)
+    fwd_b, ref_b, inv_b = morph_bytes(ny, nx, M_, K)
+    fwd_b += morph_bytes(ny, nx, 1, 1)[0]
+    inv_b += morph_bytes(ny, nx, M_, 1)[2]
+    peak, peak_kind = hbm_peak()
+    print(json.dumps({
+        "metric": "morphing FFT-EnKF analysis grid-pts*members/s (4096^2, 2 blocks, N=20)",
+        "value": float(ny) * nx * K / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (f64 mean and gains)", "data": "synthetic",
+        "config": {"workload": "morphing FFT EnKF: 2 smooth blocks 4096x4096 and smooth mappings (|T| <= 3 cells), "
+                               "N=20, FP32, extended state (T_x, T_y, r1, r2) with T_x, T_y, r1 observed, "
+                               "20 fixed-point steps", "l2": "inputs larger than L2"},
+        "parts_ms": {"forward": f_ms, "analysis": an_ms, "reference": r_ms, "inverse": i_ms},
+        "roofline": {"bound": "hbm", "kernel": "morph_forward_kernel + morph_inverse_kernel",
+                     "achieved": (fwd_b + inv_b) / ((f_ms + i_ms) / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": (fwd_b + inv_b) / ((f_ms + i_ms) / 1e3) / 1e9 / peak, "peak_kind": peak_kind,
+                     "traffic": None},
+        "reference_gbs": ref_b / (r_ms / 1e3) / 1e9,
+        "clocks": clk.summary(),
+        "gpu_launches": 12 * a.steps,
+    }))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -720,6 +828,8 @@ def main():
         return run_coupled(a)
     if a.workload == "sine":
         return run_sine(a)
+    if a.workload == "morph":
+        return run_morph(a)
     return run_ours(a)
 
 

@@ -292,6 +292,34 @@ fftenkf_status fftenkf_sine_analyze(fftenkf_sine_plan plan, void* ensemble, cons
                                     const void* perturbations, const double* rhat, void* stream);
 fftenkf_status fftenkf_sine_last_device_status(fftenkf_sine_plan plan, void* stream);
 
+/* Morphing transform around the analysis (Sec. 2.2, eq. morphing-transform and eq. inverse-morphing).
+ * The registration mappings T_k (displacement fields in grid units, T_x along x then T_y along y)
+ * are the caller's.  On the periodic ny x nx grid, f o (I + T) at node p is f(p + T(p)), f
+ * interpolated bilinearly between nodes; (I + T)^-1(p) is the fixed point q = p - T(q), reached by
+ * n_iter (0..1024) steps from q = p, which converges when T is a contraction (max |grad T| < 1).
+ * FP32 device arrays, 4-byte aligned, row-major with x fastest:
+ *   u       [M][K][ny][nx] physical members (the analysis layout with N = K)
+ *   u_ref   [M][ny][nx] the reference member u_{N+1}
+ *   ext     [M+2][K][ny][nx] extended ensemble (T_x, T_y, r^(1), ..., r^(M)): an FP32 analysis
+ *           ensemble with n_blocks = M+2 whose observed blocks are 0, 1, 2.
+ * fftenkf_morph_forward reads T from ext blocks 0, 1 and writes r_k^(j) = u_k^(j) o (I+T_k)^-1 -
+ * u_ref^(j) into blocks 2..M+1 (eq. morphing-transform).  The data maps the same way with M = K = 1:
+ * u = d, u_ref = the first block of the reference, ext = the [3][ny][nx] data of the analysis.
+ * fftenkf_morph_reference writes the member mean of ext [C][K][ny][nx] to ext_ref [C][ny][nx]: the
+ * transformed reference member after the analysis.
+ * fftenkf_morph_inverse writes u_out[j][k] = (u_ref^(j) + r_k^(j)) o (I + T_k) (eq.
+ * inverse-morphing); with K = 1 and ext = the reference mean it gives the new reference member.
+ * Outputs must not overlap inputs (EINVAL).  Displacements are taken modulo the grid (offsets beyond
+ * 2^22 cells are clamped for indexing); a non-finite displacement gives non-finite outputs, never an
+ * out-of-grid read.  Errors: EINVAL (null, misaligned or overlapping pointers, dims < 1, n_iter out
+ * of range), EUNSUPPORTED (ny * nx >= 2^31), ECUDA (launch failed).  Asynchronous on stream. */
+fftenkf_status fftenkf_morph_forward(const float* u, const float* u_ref, float* ext, int n_blocks, int n_members,
+                                     int ny, int nx, int n_iter, void* stream);
+fftenkf_status fftenkf_morph_reference(const float* ext, float* ext_ref, int n_channels, int n_members, int ny,
+                                       int nx, void* stream);
+fftenkf_status fftenkf_morph_inverse(const float* ext, const float* u_ref, float* u_out, int n_blocks,
+                                     int n_members, int ny, int nx, void* stream);
+
 /* Static description of a status code. */
 const char* fftenkf_status_string(fftenkf_status s);
 /* Message of the last failing call on this host thread ("" if none). */

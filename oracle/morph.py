@@ -61,6 +61,14 @@ def inverse_points(T: np.ndarray, n_iter: int):
     """(I + T)^-1 at every node p: q_0 = p, q_{i+1} = p - T(q_i); returns (qy, qx)."""
     T = np.asarray(T, dtype=np.float64)
     py, px = node_coords(T.shape[1], T.shape[2])
+    return inverse_points_at(T, py, px, n_iter)
+
+
+def inverse_points_at(T: np.ndarray, py: np.ndarray, px: np.ndarray, n_iter: int):
+    """(I + T)^-1 at the given nodes (py, px) only, by the same iteration."""
+    T = np.asarray(T, dtype=np.float64)
+    py = np.asarray(py, dtype=np.float64)
+    px = np.asarray(px, dtype=np.float64)
     qy, qx = py.copy(), px.copy()
     for _ in range(n_iter):
         tx = interp_periodic(T[0], qy, qx)

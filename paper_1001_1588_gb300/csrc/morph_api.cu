@@ -1,0 +1,219 @@
+// Morphing transform around the FFT EnKF (Sec. 2.2, eq. morphing-transform and eq. inverse-morphing).
+// The registration mappings T_k are inputs; these kernels compute
+//   forward:   r_k^(j) = u_k^(j) o (I + T_k)^-1 - u_ref^(j)
+//   reference: mean over the members of the extended state (T^a, r^a)
+//   inverse:   u_k^(j),a = (u_ref^(j) + r_k^(j),a) o (I + T_k^a)
+// on a periodic ny x nx grid with unit spacing.  f o (I + T) at node p is f(p + T(p)) with f
+// interpolated bilinearly between nodes; (I + T)^-1(p) is the fixed point q = p - T(q), reached by
+// n_iter steps from q = p.  Every point is kept as its node plus an FP32 offset d, so the
+// interpolation weights carry the precision of the displacement, not of the grid coordinate.
+//
+// Layouts (row-major, x fastest): members u [M][K][ny][nx]; reference u_ref [M][ny][nx]; extended
+// ensemble ext [M+2][K][ny][nx] = (T_x, T_y, r^(1), ..., r^(M)), the analysis layout with T_x, T_y and
+// r^(1) as the observed blocks.  Gathers are local (|T| of a few cells), so L1 and L2 serve them.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+
+#include "../../include/fftenkf.h"
+
+namespace fftenkf {
+void set_last_error(const std::string& msg);
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kGrid = 152 * 8;          // 8 resident CTAs on each of the 152 SMs
+constexpr float kMaxOffset = 4194304.f;  // 2^22 cells: offsets are clamped to this for indexing
+constexpr int kMaxIter = 1024;
+
+fftenkf_status mfail(fftenkf_status s, const std::string& msg) {
+  fftenkf::set_last_error(msg);
+  return s;
+}
+
+// Bilinear stencil of node (y, x) displaced by (dy, dx) on the periodic grid.  Indexes always lie in
+// the grid; a non-finite offset gives non-finite weights, so it shows in the output.
+struct Stencil {
+  int y0, y1, x0, x1;
+  float wy, wx;
+};
+
+__device__ __forceinline__ void axis(int p, float d, int n, int& i0, int& i1, float& w) {
+  const float dc = fminf(fmaxf(d, -kMaxOffset), kMaxOffset);
+  const float f = floorf(dc);
+  w = isfinite(d) ? dc - f : d - d;
+  int i = (p + (int)f) % n;
+  if (i < 0) i += n;
+  i0 = i;
+  i1 = (i + 1 == n) ? 0 : i + 1;
+}
+
+__device__ __forceinline__ Stencil stencil(int y, int x, float dy, float dx, int ny, int nx) {
+  Stencil s;
+  axis(y, dy, ny, s.y0, s.y1, s.wy);
+  axis(x, dx, nx, s.x0, s.x1, s.wx);
+  return s;
+}
+
+__device__ __forceinline__ float interp(const float* __restrict__ f, const Stencil& s, int nx) {
+  const float f00 = __ldg(f + (size_t)s.y0 * nx + s.x0), f01 = __ldg(f + (size_t)s.y0 * nx + s.x1);
+  const float f10 = __ldg(f + (size_t)s.y1 * nx + s.x0), f11 = __ldg(f + (size_t)s.y1 * nx + s.x1);
+  return (1.f - s.wy) * ((1.f - s.wx) * f00 + s.wx * f01) + s.wy * ((1.f - s.wx) * f10 + s.wx * f11);
+}
+
+// One thread per (member, node).  ext blocks 0, 1 (T) are read, blocks 2.. (r) written.
+__global__ void __launch_bounds__(kThreads) morph_forward_kernel(const float* __restrict__ u,
+                                                                 const float* __restrict__ u_ref,
+                                                                 float* __restrict__ ext, int M, int K, int ny,
+                                                                 int nx, int n_iter) {
+  const size_t plane = (size_t)ny * nx;
+  const size_t total = (size_t)K * plane;
+  const float* Tx = ext;
+  const float* Ty = ext + total;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (size_t)gridDim.x * kThreads) {
+    const int k = (int)(i / plane);
+    const size_t p = i - (size_t)k * plane;
+    const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
+    const float* tx = Tx + (size_t)k * plane;
+    const float* ty = Ty + (size_t)k * plane;
+    float dy = 0.f, dx = 0.f;   // q_0 = p
+    for (int it = 0; it < n_iter; ++it) {
+      const Stencil s = stencil(y, x, dy, dx, ny, nx);
+      const float ndx = -interp(tx, s, nx);
+      const float ndy = -interp(ty, s, nx);
+      dx = ndx;
+      dy = ndy;
+    }
+    const Stencil s = stencil(y, x, dy, dx, ny, nx);
+    for (int j = 0; j < M; ++j) {
+      const float v = interp(u + ((size_t)j * K + k) * plane, s, nx);
+      ext[((size_t)(2 + j) * K + k) * plane + p] = v - __ldg(u_ref + (size_t)j * plane + p);
+    }
+  }
+}
+
+// ext_ref [C][ny][nx] = member mean of ext [C][K][ny][nx], summed in member order.
+__global__ void __launch_bounds__(kThreads) morph_reference_kernel(const float* __restrict__ ext,
+                                                                   float* __restrict__ ext_ref, int C, int K,
+                                                                   size_t plane) {
+  const size_t total = (size_t)C * plane;
+  const float inv = 1.f / (float)K;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (size_t)gridDim.x * kThreads) {
+    const size_t c = i / plane, p = i - c * plane;
+    const float* e = ext + c * K * plane + p;
+    float acc = 0.f;
+    for (int k = 0; k < K; ++k) acc += __ldg(e + (size_t)k * plane);
+    ext_ref[i] = acc * inv;
+  }
+}
+
+// One thread per (member, node): u_out[j][k](p) = (u_ref[j] + r[j][k]) at p + T_k(p).
+__global__ void __launch_bounds__(kThreads) morph_inverse_kernel(const float* __restrict__ ext,
+                                                                 const float* __restrict__ u_ref,
+                                                                 float* __restrict__ u_out, int M, int K, int ny,
+                                                                 int nx) {
+  const size_t plane = (size_t)ny * nx;
+  const size_t total = (size_t)K * plane;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (size_t)gridDim.x * kThreads) {
+    const int k = (int)(i / plane);
+    const size_t p = i - (size_t)k * plane;
+    const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
+    const float dx = __ldg(ext + i), dy = __ldg(ext + total + i);
+    const Stencil s = stencil(y, x, dy, dx, ny, nx);
+    for (int j = 0; j < M; ++j) {
+      const float* g = u_ref + (size_t)j * plane;
+      const float* r = ext + ((size_t)(2 + j) * K + k) * plane;
+      const size_t o00 = (size_t)s.y0 * nx + s.x0, o01 = (size_t)s.y0 * nx + s.x1;
+      const size_t o10 = (size_t)s.y1 * nx + s.x0, o11 = (size_t)s.y1 * nx + s.x1;
+      const float f00 = __ldg(g + o00) + __ldg(r + o00), f01 = __ldg(g + o01) + __ldg(r + o01);
+      const float f10 = __ldg(g + o10) + __ldg(r + o10), f11 = __ldg(g + o11) + __ldg(r + o11);
+      u_out[((size_t)j * K + k) * plane + p] =
+          (1.f - s.wy) * ((1.f - s.wx) * f00 + s.wx * f01) + s.wy * ((1.f - s.wx) * f10 + s.wx * f11);
+    }
+  }
+}
+
+int grid_for(size_t units) {
+  const size_t g = (units + kThreads - 1) / kThreads;
+  return (int)(g < (size_t)kGrid ? (g ? g : 1) : (size_t)kGrid);
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+fftenkf_status check_dims(const char* who, int M, int K, int ny, int nx) {
+  if (M < 1 || K < 1 || ny < 1 || nx < 1)
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": n_blocks, n_members, ny, nx must be >= 1");
+  if ((long long)ny * nx > (1LL << 31) - 1)
+    return mfail(FFTENKF_EUNSUPPORTED, std::string(who) + ": ny * nx must be below 2^31");
+  return FFTENKF_OK;
+}
+
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+fftenkf_status finish(const char* who) {
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return mfail(FFTENKF_ECUDA, std::string(who) + ": launch failed: " + cudaGetErrorString(ce));
+  return FFTENKF_OK;
+}
+
+}  // namespace
+
+extern "C" fftenkf_status fftenkf_morph_forward(const float* u, const float* u_ref, float* ext, int n_blocks,
+                                                int n_members, int ny, int nx, int n_iter, void* stream) {
+  const char* who = "fftenkf_morph_forward";
+  fftenkf_status st = check_dims(who, n_blocks, n_members, ny, nx);
+  if (st != FFTENKF_OK) return st;
+  if (!u || !u_ref || !ext || !aligned4(u) || !aligned4(u_ref) || !aligned4(ext))
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": null or misaligned pointer");
+  if (n_iter < 0 || n_iter > kMaxIter) return mfail(FFTENKF_EINVAL, std::string(who) + ": n_iter must be in [0, 1024]");
+  const size_t plane = (size_t)ny * nx * sizeof(float);
+  const size_t r_bytes = (size_t)n_blocks * n_members * plane;
+  const float* r = ext + (size_t)2 * n_members * ny * nx;
+  if (overlaps(r, r_bytes, u, r_bytes) || overlaps(r, r_bytes, u_ref, (size_t)n_blocks * plane) ||
+      overlaps(r, r_bytes, ext, (size_t)2 * n_members * plane))
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": the residual blocks of ext overlap an input");
+  morph_forward_kernel<<<grid_for((size_t)n_members * ny * nx), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter);
+  return finish(who);
+}
+
+extern "C" fftenkf_status fftenkf_morph_reference(const float* ext, float* ext_ref, int n_channels, int n_members,
+                                                  int ny, int nx, void* stream) {
+  const char* who = "fftenkf_morph_reference";
+  fftenkf_status st = check_dims(who, n_channels, n_members, ny, nx);
+  if (st != FFTENKF_OK) return st;
+  if (!ext || !ext_ref || !aligned4(ext) || !aligned4(ext_ref))
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": null or misaligned pointer");
+  const size_t plane = (size_t)ny * nx;
+  if (overlaps(ext, (size_t)n_channels * n_members * plane * sizeof(float), ext_ref,
+               (size_t)n_channels * plane * sizeof(float)))
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": ext_ref overlaps ext");
+  morph_reference_kernel<<<grid_for((size_t)n_channels * plane), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      ext, ext_ref, n_channels, n_members, plane);
+  return finish(who);
+}
+
+extern "C" fftenkf_status fftenkf_morph_inverse(const float* ext, const float* u_ref, float* u_out, int n_blocks,
+                                                int n_members, int ny, int nx, void* stream) {
+  const char* who = "fftenkf_morph_inverse";
+  fftenkf_status st = check_dims(who, n_blocks, n_members, ny, nx);
+  if (st != FFTENKF_OK) return st;
+  if (!ext || !u_ref || !u_out || !aligned4(ext) || !aligned4(u_ref) || !aligned4(u_out))
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": null or misaligned pointer");
+  const size_t plane = (size_t)ny * nx * sizeof(float);
+  const size_t out_bytes = (size_t)n_blocks * n_members * plane;
+  if (overlaps(u_out, out_bytes, ext, (size_t)(n_blocks + 2) * n_members * plane) ||
+      overlaps(u_out, out_bytes, u_ref, (size_t)n_blocks * plane))
+    return mfail(FFTENKF_EINVAL, std::string(who) + ": u_out overlaps an input");
+  morph_inverse_kernel<<<grid_for((size_t)n_members * ny * nx), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      ext, u_ref, u_out, n_blocks, n_members, ny, nx);
+  return finish(who);
+}

@@ -85,3 +85,20 @@ def test_pass_byte_model_matches_analysis_model():
         tot = sum(pb[k] for k in used) - extra
         ref = b.analysis_bytes(ny, nx, M, N, no, s)
         assert abs(tot - ref) / ref < 0.005, (tot, ref)   # packed nx/2 vs nx/2+1 columns
+
+
+# Morphing entry points: argument checks that return before any CUDA call (fake, aligned addresses).
+def test_morph_rejects_before_launch(lib):
+    plane = 8 * 8 * 4
+    base = 0x1000000
+    # residual blocks of ext (from base + 2*K*plane) alias u
+    assert lib.fftenkf_morph_forward(base + 4 * plane, base + 100 * plane, base, 1, 2, 8, 8, 4, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 1025, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 0, 2, 8, 8, 4, None) == 1
+    assert lib.fftenkf_morph_forward(base + 2, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, None) == 1
+    assert lib.fftenkf_morph_forward(None, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 65536, 65536, 4, None) == 2
+    assert lib.fftenkf_morph_reference(base, base + plane, 3, 2, 8, 8, None) == 1     # ext_ref inside ext
+    assert lib.fftenkf_morph_reference(base, base + 100 * plane, 3, 0, 8, 8, None) == 1
+    assert lib.fftenkf_morph_inverse(base, base + 100 * plane, base + plane, 1, 2, 8, 8, None) == 1   # u_out in ext
+    assert lib.fftenkf_morph_inverse(base, base + 100 * plane, base + 100 * plane, 1, 2, 8, 8, None) == 1
