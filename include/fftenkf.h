@@ -312,7 +312,8 @@ fftenkf_status fftenkf_sine_last_device_status(fftenkf_sine_plan plan, void* str
  * Outputs must not overlap inputs (EINVAL).  Displacements are taken modulo the grid (offsets beyond
  * 2^22 cells are clamped for indexing); a non-finite displacement gives non-finite outputs, never an
  * out-of-grid read.  Errors: EINVAL (null, misaligned or overlapping pointers, dims < 1, n_iter out
- * of range), EUNSUPPORTED (ny * nx >= 2^31), ECUDA (launch failed).  Asynchronous on stream. */
+ * of range), EUNSUPPORTED (ny * nx > 2^31 - 2^20, n_members > 65535), ECUDA (launch
+ * failed).  Asynchronous on stream. */
 fftenkf_status fftenkf_morph_forward(const float* u, const float* u_ref, float* ext, int n_blocks, int n_members,
                                      int ny, int nx, int n_iter, void* stream);
 fftenkf_status fftenkf_morph_reference(const float* ext, float* ext_ref, int n_channels, int n_members, int ny,

@@ -37,9 +37,10 @@ fftenkf_status mfail(fftenkf_status s, const std::string& msg) {
 }
 
 // Bilinear stencil of node (y, x) displaced by (dy, dx) on the periodic grid.  Indexes always lie in
-// the grid; a non-finite offset gives non-finite weights, so it shows in the output.
+// the grid; a non-finite offset gives non-finite weights, so it shows in the output.  Plane offsets
+// are 32-bit (ny * nx < 2^31).
 struct Stencil {
-  int y0, y1, x0, x1;
+  int r0, r1, x0, x1;   // row offsets y * nx and columns
   float wy, wx;
 };
 
@@ -47,51 +48,57 @@ __device__ __forceinline__ void axis(int p, float d, int n, int& i0, int& i1, fl
   const float dc = fminf(fmaxf(d, -kMaxOffset), kMaxOffset);
   const float f = floorf(dc);
   w = isfinite(d) ? dc - f : d - d;
-  int i = (p + (int)f) % n;
-  if (i < 0) i += n;
+  int i = p + (int)f;
+  if ((unsigned)i >= (unsigned)n) {   // off the grid: wrap (rare for offsets of a few cells)
+    i %= n;
+    if (i < 0) i += n;
+  }
   i0 = i;
   i1 = (i + 1 == n) ? 0 : i + 1;
 }
 
 __device__ __forceinline__ Stencil stencil(int y, int x, float dy, float dx, int ny, int nx) {
   Stencil s;
-  axis(y, dy, ny, s.y0, s.y1, s.wy);
+  int y0, y1;
+  axis(y, dy, ny, y0, y1, s.wy);
   axis(x, dx, nx, s.x0, s.x1, s.wx);
+  s.r0 = y0 * nx;
+  s.r1 = y1 * nx;
   return s;
 }
 
-__device__ __forceinline__ float interp(const float* __restrict__ f, const Stencil& s, int nx) {
-  const float f00 = __ldg(f + (size_t)s.y0 * nx + s.x0), f01 = __ldg(f + (size_t)s.y0 * nx + s.x1);
-  const float f10 = __ldg(f + (size_t)s.y1 * nx + s.x0), f11 = __ldg(f + (size_t)s.y1 * nx + s.x1);
+__device__ __forceinline__ float interp(const float* __restrict__ f, const Stencil& s) {
+  const float f00 = __ldg(f + s.r0 + s.x0), f01 = __ldg(f + s.r0 + s.x1);
+  const float f10 = __ldg(f + s.r1 + s.x0), f11 = __ldg(f + s.r1 + s.x1);
   return (1.f - s.wy) * ((1.f - s.wx) * f00 + s.wx * f01) + s.wy * ((1.f - s.wx) * f10 + s.wx * f11);
 }
 
-// One thread per (member, node).  ext blocks 0, 1 (T) are read, blocks 2.. (r) written.
-__global__ void __launch_bounds__(kThreads) morph_forward_kernel(const float* __restrict__ u,
+// grid (x: nodes of one plane, grid-stride; y: member k).  ext blocks 0, 1 (T) are read, blocks 2..
+// (r) written.  The iteration stops early once an iterate repeats exactly: every later one would be
+// the same, so the result equals that of all n_iter steps.
+__global__ void __launch_bounds__(kThreads, 4) morph_forward_kernel(const float* __restrict__ u,
                                                                  const float* __restrict__ u_ref,
                                                                  float* __restrict__ ext, int M, int K, int ny,
                                                                  int nx, int n_iter) {
-  const size_t plane = (size_t)ny * nx;
-  const size_t total = (size_t)K * plane;
-  const float* Tx = ext;
-  const float* Ty = ext + total;
-  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (size_t)gridDim.x * kThreads) {
-    const int k = (int)(i / plane);
-    const size_t p = i - (size_t)k * plane;
-    const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
-    const float* tx = Tx + (size_t)k * plane;
-    const float* ty = Ty + (size_t)k * plane;
+  const int plane = ny * nx;
+  const int k = blockIdx.y;
+  const float* tx = ext + (size_t)k * plane;
+  const float* ty = ext + ((size_t)K + k) * plane;
+  for (int p = blockIdx.x * kThreads + threadIdx.x; p < plane; p += gridDim.x * kThreads) {
+    const int y = p / nx, x = p - y * nx;
     float dy = 0.f, dx = 0.f;   // q_0 = p
     for (int it = 0; it < n_iter; ++it) {
       const Stencil s = stencil(y, x, dy, dx, ny, nx);
-      const float ndx = -interp(tx, s, nx);
-      const float ndy = -interp(ty, s, nx);
+      const float ndx = -interp(tx, s);
+      const float ndy = -interp(ty, s);
+      const bool same = (ndx == dx) && (ndy == dy);
       dx = ndx;
       dy = ndy;
+      if (same) break;
     }
     const Stencil s = stencil(y, x, dy, dx, ny, nx);
     for (int j = 0; j < M; ++j) {
-      const float v = interp(u + ((size_t)j * K + k) * plane, s, nx);
+      const float v = interp(u + ((size_t)j * K + k) * plane, s);
       ext[((size_t)(2 + j) * K + k) * plane + p] = v - __ldg(u_ref + (size_t)j * plane + p);
     }
   }
@@ -112,30 +119,39 @@ __global__ void __launch_bounds__(kThreads) morph_reference_kernel(const float* 
   }
 }
 
-// One thread per (member, node): u_out[j][k](p) = (u_ref[j] + r[j][k]) at p + T_k(p).
-__global__ void __launch_bounds__(kThreads) morph_inverse_kernel(const float* __restrict__ ext,
+// grid (x: nodes of one plane, grid-stride; y: member k): u_out[j][k](p) = (u_ref[j] + r[j][k]) at
+// p + T_k(p).
+__global__ void __launch_bounds__(kThreads, 4) morph_inverse_kernel(const float* __restrict__ ext,
                                                                  const float* __restrict__ u_ref,
                                                                  float* __restrict__ u_out, int M, int K, int ny,
                                                                  int nx) {
-  const size_t plane = (size_t)ny * nx;
-  const size_t total = (size_t)K * plane;
-  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (size_t)gridDim.x * kThreads) {
-    const int k = (int)(i / plane);
-    const size_t p = i - (size_t)k * plane;
-    const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
-    const float dx = __ldg(ext + i), dy = __ldg(ext + total + i);
-    const Stencil s = stencil(y, x, dy, dx, ny, nx);
+  const int plane = ny * nx;
+  const int k = blockIdx.y;
+  const float* tx = ext + (size_t)k * plane;
+  const float* ty = ext + ((size_t)K + k) * plane;
+  for (int p = blockIdx.x * kThreads + threadIdx.x; p < plane; p += gridDim.x * kThreads) {
+    const int y = p / nx, x = p - y * nx;
+    const Stencil s = stencil(y, x, __ldg(ty + p), __ldg(tx + p), ny, nx);
     for (int j = 0; j < M; ++j) {
       const float* g = u_ref + (size_t)j * plane;
       const float* r = ext + ((size_t)(2 + j) * K + k) * plane;
-      const size_t o00 = (size_t)s.y0 * nx + s.x0, o01 = (size_t)s.y0 * nx + s.x1;
-      const size_t o10 = (size_t)s.y1 * nx + s.x0, o11 = (size_t)s.y1 * nx + s.x1;
-      const float f00 = __ldg(g + o00) + __ldg(r + o00), f01 = __ldg(g + o01) + __ldg(r + o01);
-      const float f10 = __ldg(g + o10) + __ldg(r + o10), f11 = __ldg(g + o11) + __ldg(r + o11);
+      const float f00 = __ldg(g + s.r0 + s.x0) + __ldg(r + s.r0 + s.x0);
+      const float f01 = __ldg(g + s.r0 + s.x1) + __ldg(r + s.r0 + s.x1);
+      const float f10 = __ldg(g + s.r1 + s.x0) + __ldg(r + s.r1 + s.x0);
+      const float f11 = __ldg(g + s.r1 + s.x1) + __ldg(r + s.r1 + s.x1);
       u_out[((size_t)j * K + k) * plane + p] =
           (1.f - s.wy) * ((1.f - s.wx) * f00 + s.wx * f01) + s.wy * ((1.f - s.wx) * f10 + s.wx * f11);
     }
   }
+}
+
+// Launch shape of the per-member kernels: member k on grid.y, about kGrid CTAs in all.
+dim3 member_grid(int plane, int K) {
+  int gx = (kGrid + K - 1) / K;
+  const int need = (plane + kThreads - 1) / kThreads;
+  if (gx > need) gx = need;
+  if (gx < 1) gx = 1;
+  return dim3(gx, K);
 }
 
 int grid_for(size_t units) {
@@ -151,8 +167,9 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 fftenkf_status check_dims(const char* who, int M, int K, int ny, int nx) {
   if (M < 1 || K < 1 || ny < 1 || nx < 1)
     return mfail(FFTENKF_EINVAL, std::string(who) + ": n_blocks, n_members, ny, nx must be >= 1");
-  if ((long long)ny * nx > (1LL << 31) - 1)
-    return mfail(FFTENKF_EUNSUPPORTED, std::string(who) + ": ny * nx must be below 2^31");
+  if (K > 65535) return mfail(FFTENKF_EUNSUPPORTED, std::string(who) + ": n_members must be at most 65535");
+  if ((long long)ny * nx > (1LL << 31) - (1LL << 20))
+    return mfail(FFTENKF_EUNSUPPORTED, std::string(who) + ": ny * nx must be at most 2^31 - 2^20");
   return FFTENKF_OK;
 }
 
@@ -180,7 +197,7 @@ extern "C" fftenkf_status fftenkf_morph_forward(const float* u, const float* u_r
   if (overlaps(r, r_bytes, u, r_bytes) || overlaps(r, r_bytes, u_ref, (size_t)n_blocks * plane) ||
       overlaps(r, r_bytes, ext, (size_t)2 * n_members * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": the residual blocks of ext overlap an input");
-  morph_forward_kernel<<<grid_for((size_t)n_members * ny * nx), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_forward_kernel<<<member_grid(ny * nx, n_members), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter);
   return finish(who);
 }
@@ -213,7 +230,7 @@ extern "C" fftenkf_status fftenkf_morph_inverse(const float* ext, const float* u
   if (overlaps(u_out, out_bytes, ext, (size_t)(n_blocks + 2) * n_members * plane) ||
       overlaps(u_out, out_bytes, u_ref, (size_t)n_blocks * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": u_out overlaps an input");
-  morph_inverse_kernel<<<grid_for((size_t)n_members * ny * nx), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_inverse_kernel<<<member_grid(ny * nx, n_members), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       ext, u_ref, u_out, n_blocks, n_members, ny, nx);
   return finish(who);
 }
