@@ -296,7 +296,9 @@ fftenkf_status fftenkf_sine_last_device_status(fftenkf_sine_plan plan, void* str
  * The registration mappings T_k (displacement fields in grid units, T_x along x then T_y along y)
  * are the caller's.  On the periodic ny x nx grid, f o (I + T) at node p is f(p + T(p)), f
  * interpolated bilinearly between nodes; (I + T)^-1(p) is the fixed point q = p - T(q), reached by
- * n_iter (0..1024) steps from q = p, which converges when T is a contraction (max |grad T| < 1).
+ * at most n_iter (0..1024) steps from q = p, which converges when T is a contraction (max |grad T|
+ * < 1); a node stops after the first step that moves it by at most tol cells in each component
+ * (tol = 0: only when an iterate repeats exactly, the result of all n_iter steps).
  * FP32 device arrays, 4-byte aligned, row-major with x fastest:
  *   u       [M][K][ny][nx] physical members (the analysis layout with N = K)
  *   u_ref   [M][ny][nx] the reference member u_{N+1}
@@ -312,10 +314,10 @@ fftenkf_status fftenkf_sine_last_device_status(fftenkf_sine_plan plan, void* str
  * Outputs must not overlap inputs (EINVAL).  Displacements are taken modulo the grid (offsets beyond
  * 2^22 cells are clamped for indexing); a non-finite displacement gives non-finite outputs, never an
  * out-of-grid read.  Errors: EINVAL (null, misaligned or overlapping pointers, dims < 1, n_iter out
- * of range), EUNSUPPORTED (ny * nx > 2^31 - 2^20, n_members > 65535), ECUDA (launch
+ * of range, tol negative or not finite), EUNSUPPORTED (ny * nx > 2^31 - 2^20, n_members > 65535), ECUDA (launch
  * failed).  Asynchronous on stream. */
 fftenkf_status fftenkf_morph_forward(const float* u, const float* u_ref, float* ext, int n_blocks, int n_members,
-                                     int ny, int nx, int n_iter, void* stream);
+                                     int ny, int nx, int n_iter, float tol, void* stream);
 fftenkf_status fftenkf_morph_reference(const float* ext, float* ext_ref, int n_channels, int n_members, int ny,
                                        int nx, void* stream);
 fftenkf_status fftenkf_morph_inverse(const float* ext, const float* u_ref, float* u_out, int n_blocks,

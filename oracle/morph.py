@@ -11,7 +11,8 @@ Readings (the paper fixes none of them):
   * Composition f o (I + T) at node p is f(p + T(p)), with f evaluated between nodes by bilinear
     interpolation on the periodic grid.
   * (I + T)^-1(p) is the point q with q + T(q) = p, found by the fixed-point iteration
-    q_0 = p, q_{i+1} = p - T(q_i) (T interpolated bilinearly at q_i), n_iter steps.  It converges
+    q_0 = p, q_{i+1} = p - T(q_i) (T interpolated bilinearly at q_i), at most n_iter steps, a point
+    stopping after the first step that moves it by at most tol in each component.  It converges
     when T is a contraction, which the registration's conditions T ~ 0, grad T ~ 0 ask for.
   * The extended state of member k keeps the analysis layout: blocks (T_x, T_y, r^(1), ..., r^(M)),
     and the extended data is (T_0x, T_0y, r_0^(1)).
@@ -57,27 +58,36 @@ def compose(f: np.ndarray, T: np.ndarray) -> np.ndarray:
     return interp_periodic(f, py + T[1], px + T[0])
 
 
-def inverse_points(T: np.ndarray, n_iter: int):
+def inverse_points(T: np.ndarray, n_iter: int, tol: float = 0.0):
     """(I + T)^-1 at every node p: q_0 = p, q_{i+1} = p - T(q_i); returns (qy, qx)."""
     T = np.asarray(T, dtype=np.float64)
     py, px = node_coords(T.shape[1], T.shape[2])
-    return inverse_points_at(T, py, px, n_iter)
+    return inverse_points_at(T, py, px, n_iter, tol)
 
 
-def inverse_points_at(T: np.ndarray, py: np.ndarray, px: np.ndarray, n_iter: int):
-    """(I + T)^-1 at the given nodes (py, px) only, by the same iteration."""
+def inverse_points_at(T: np.ndarray, py: np.ndarray, px: np.ndarray, n_iter: int, tol: float = 0.0):
+    """(I + T)^-1 at the given nodes (py, px) only, by the same iteration.  A point stops after the
+    first step that moves it by at most tol in each component (tol = 0: only when the iterate
+    repeats, which changes nothing), else after n_iter steps."""
     T = np.asarray(T, dtype=np.float64)
     py = np.asarray(py, dtype=np.float64)
     px = np.asarray(px, dtype=np.float64)
     qy, qx = py.copy(), px.copy()
+    active = np.ones(qy.shape, dtype=bool)
     for _ in range(n_iter):
+        if not active.any():
+            break
         tx = interp_periodic(T[0], qy, qx)
         ty = interp_periodic(T[1], qy, qx)
-        qy, qx = py - ty, px - tx
+        ny_, nx_ = py - ty, px - tx
+        done = (np.abs(ny_ - qy) <= tol) & (np.abs(nx_ - qx) <= tol)
+        qy = np.where(active, ny_, qy)
+        qx = np.where(active, nx_, qx)
+        active &= ~done
     return qy, qx
 
 
-def morph_forward(u: np.ndarray, u_ref: np.ndarray, T: np.ndarray, n_iter: int) -> np.ndarray:
+def morph_forward(u: np.ndarray, u_ref: np.ndarray, T: np.ndarray, n_iter: int, tol: float = 0.0) -> np.ndarray:
     """Residuals r [M][K][ny][nx] of the members u [M][K][ny][nx] against u_ref [M][ny][nx] under
     the mappings T [2][K][ny][nx] (eq. morphing-transform)."""
     u = np.asarray(u, dtype=np.float64)
@@ -86,7 +96,7 @@ def morph_forward(u: np.ndarray, u_ref: np.ndarray, T: np.ndarray, n_iter: int) 
     M, K = u.shape[0], u.shape[1]
     r = np.empty_like(u)
     for k in range(K):
-        qy, qx = inverse_points(T[:, k], n_iter)
+        qy, qx = inverse_points(T[:, k], n_iter, tol)
         for j in range(M):
             r[j, k] = interp_periodic(u[j, k], qy, qx) - u_ref[j]
     return r

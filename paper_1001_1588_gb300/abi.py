@@ -84,7 +84,8 @@ _SIGNATURES = [
     ("fftenkf_sine_estimate_spectrum", ctypes.c_int, [ctypes.c_void_p] * 4),
     ("fftenkf_sine_analyze", ctypes.c_int, [ctypes.c_void_p] * 6),
     ("fftenkf_sine_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
-    ("fftenkf_morph_forward", ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int] * 5 + [ctypes.c_void_p]),
+    ("fftenkf_morph_forward", ctypes.c_int,
+     [ctypes.c_void_p] * 3 + [ctypes.c_int] * 5 + [ctypes.c_float, ctypes.c_void_p]),
     ("fftenkf_morph_reference", ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
     ("fftenkf_morph_inverse", ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
     ("fftenkf_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -211,8 +212,8 @@ def fftenkf_sine_last_device_status(plan, stream=None) -> int:
     return lib().fftenkf_sine_last_device_status(plan, stream)
 
 
-def fftenkf_morph_forward(u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter, stream=None):
-    check(lib().fftenkf_morph_forward(_p(u), _p(u_ref), _p(ext), n_blocks, n_members, ny, nx, n_iter, stream),
+def fftenkf_morph_forward(u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter, tol=0.0, stream=None):
+    check(lib().fftenkf_morph_forward(_p(u), _p(u_ref), _p(ext), n_blocks, n_members, ny, nx, n_iter, tol, stream),
           "fftenkf_morph_forward")
 
 

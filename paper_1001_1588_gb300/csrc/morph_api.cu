@@ -74,12 +74,13 @@ __device__ __forceinline__ float interp(const float* __restrict__ f, const Stenc
 }
 
 // grid (x: nodes of one plane, grid-stride; y: member k).  ext blocks 0, 1 (T) are read, blocks 2..
-// (r) written.  The iteration stops early once an iterate repeats exactly: every later one would be
-// the same, so the result equals that of all n_iter steps.
+// (r) written.  The iteration stops after the first step that moves the point by at most tol cells
+// in each component (tol = 0: once an iterate repeats exactly, which gives the result of all n_iter
+// steps), else after n_iter steps.
 __global__ void __launch_bounds__(kThreads, 4) morph_forward_kernel(const float* __restrict__ u,
                                                                  const float* __restrict__ u_ref,
                                                                  float* __restrict__ ext, int M, int K, int ny,
-                                                                 int nx, int n_iter) {
+                                                                 int nx, int n_iter, float tol) {
   const int plane = ny * nx;
   const int k = blockIdx.y;
   const float* tx = ext + (size_t)k * plane;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 4) morph_forward_kernel(const float*
       const Stencil s = stencil(y, x, dy, dx, ny, nx);
       const float ndx = -interp(tx, s);
       const float ndy = -interp(ty, s);
-      const bool same = (ndx == dx) && (ndy == dy);
+      const bool same = (fabsf(ndx - dx) <= tol) && (fabsf(ndy - dy) <= tol);
       dx = ndx;
       dy = ndy;
       if (same) break;
@@ -184,13 +185,15 @@ fftenkf_status finish(const char* who) {
 }  // namespace
 
 extern "C" fftenkf_status fftenkf_morph_forward(const float* u, const float* u_ref, float* ext, int n_blocks,
-                                                int n_members, int ny, int nx, int n_iter, void* stream) {
+                                                int n_members, int ny, int nx, int n_iter, float tol,
+                                                void* stream) {
   const char* who = "fftenkf_morph_forward";
   fftenkf_status st = check_dims(who, n_blocks, n_members, ny, nx);
   if (st != FFTENKF_OK) return st;
   if (!u || !u_ref || !ext || !aligned4(u) || !aligned4(u_ref) || !aligned4(ext))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": null or misaligned pointer");
   if (n_iter < 0 || n_iter > kMaxIter) return mfail(FFTENKF_EINVAL, std::string(who) + ": n_iter must be in [0, 1024]");
+  if (!(tol >= 0.f) || !std::isfinite(tol)) return mfail(FFTENKF_EINVAL, std::string(who) + ": tol must be finite and >= 0");
   const size_t plane = (size_t)ny * nx * sizeof(float);
   const size_t r_bytes = (size_t)n_blocks * n_members * plane;
   const float* r = ext + (size_t)2 * n_members * ny * nx;
@@ -198,7 +201,7 @@ extern "C" fftenkf_status fftenkf_morph_forward(const float* u, const float* u_r
       overlaps(r, r_bytes, ext, (size_t)2 * n_members * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": the residual blocks of ext overlap an input");
   morph_forward_kernel<<<member_grid(ny * nx, n_members), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter);
+      u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter, tol);
   return finish(who);
 }
 

@@ -92,12 +92,14 @@ def test_morph_rejects_before_launch(lib):
     plane = 8 * 8 * 4
     base = 0x1000000
     # residual blocks of ext (from base + 2*K*plane) alias u
-    assert lib.fftenkf_morph_forward(base + 4 * plane, base + 100 * plane, base, 1, 2, 8, 8, 4, None) == 1
-    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 1025, None) == 1
-    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 0, 2, 8, 8, 4, None) == 1
-    assert lib.fftenkf_morph_forward(base + 2, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, None) == 1
-    assert lib.fftenkf_morph_forward(None, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, None) == 1
-    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 65536, 65536, 4, None) == 2
+    assert lib.fftenkf_morph_forward(base + 4 * plane, base + 100 * plane, base, 1, 2, 8, 8, 4, 0.0, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 1025, 0.0, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 0, 2, 8, 8, 4, 0.0, None) == 1
+    assert lib.fftenkf_morph_forward(base + 2, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, 0.0, None) == 1
+    assert lib.fftenkf_morph_forward(None, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, 0.0, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 65536, 65536, 4, 0.0, None) == 2
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, -1.0, None) == 1
+    assert lib.fftenkf_morph_forward(base, base + 100 * plane, base + 10 * plane, 1, 2, 8, 8, 4, float("nan"), None) == 1
     assert lib.fftenkf_morph_reference(base, base + plane, 3, 2, 8, 8, None) == 1     # ext_ref inside ext
     assert lib.fftenkf_morph_reference(base, base + 100 * plane, 3, 0, 8, 8, None) == 1
     assert lib.fftenkf_morph_inverse(base, base + 100 * plane, base + plane, 1, 2, 8, 8, None) == 1   # u_out in ext

@@ -49,21 +49,22 @@ def _inputs(M, K, ny, nx, amp, seed):
     return u, u_ref, T
 
 
-def _gpu_forward(u, u_ref, T, n_iter):
+def _gpu_forward(u, u_ref, T, n_iter, tol=0.0):
     M, K, ny, nx = u.shape
     ext = torch.zeros((M + 2, K, ny, nx), dtype=torch.float32, device="cuda")
     ext[:2] = _dev(T)
-    _abi().fftenkf_morph_forward(_dev(u), _dev(u_ref), ext, M, K, ny, nx, n_iter)
+    _abi().fftenkf_morph_forward(_dev(u), _dev(u_ref), ext, M, K, ny, nx, n_iter, tol)
     torch.cuda.synchronize()
     return ext.cpu().numpy()
 
 
-@pytest.mark.parametrize("M,K,ny,nx,n_iter", [(2, 5, 96, 200, 20), (1, 3, 37, 61, 8), (3, 1, 8, 8, 0)])
-def test_forward_matches_oracle(M, K, ny, nx, n_iter):
+@pytest.mark.parametrize("M,K,ny,nx,n_iter,tol", [(2, 5, 96, 200, 20, 0.0), (1, 3, 37, 61, 8, 0.0),
+                                                  (3, 1, 8, 8, 0, 0.0), (2, 4, 128, 160, 20, 1e-5)])
+def test_forward_matches_oracle(M, K, ny, nx, n_iter, tol):
     u, u_ref, T = _inputs(M, K, ny, nx, 2.5, 100 + M)
-    ext = _gpu_forward(u, u_ref, T, n_iter)
+    ext = _gpu_forward(u, u_ref, T, n_iter, tol)
     np.testing.assert_array_equal(ext[:2], T)   # the mappings are left as they were
-    ref = morph.morph_forward(u, u_ref, T, n_iter)
+    ref = morph.morph_forward(u, u_ref, T, n_iter, tol)
     assert _rel(ext[2:], ref) <= TOL
     assert np.abs(ext[2:] - ref).max() <= ATOL
 
@@ -120,10 +121,10 @@ def test_morphing_enkf_chain_matches_oracle():
     ext = torch.zeros((M + 2, N, ny, nx), dtype=torch.float32, device="cuda")
     ext[:2] = _dev(T)
     ur = _dev(u_ref)
-    abi.fftenkf_morph_forward(_dev(u), ur, ext, M, N, ny, nx, 20)
+    abi.fftenkf_morph_forward(_dev(u), ur, ext, M, N, ny, nx, 20, 1e-5)
     data = torch.zeros((3, 1, ny, nx), dtype=torch.float32, device="cuda")
     data[:2] = _dev(T0)
-    abi.fftenkf_morph_forward(_dev(d), ur[:1], data, 1, 1, ny, nx, 20)
+    abi.fftenkf_morph_forward(_dev(d), ur[:1], data, 1, 1, ny, nx, 20, 1e-5)
     plan = torch_api.Plan(ny, nx, M + 2, N, torch.float32, observed)
     plan.analyze(ext, data.reshape(3, ny, nx), _dev(pert), torch.from_numpy(rhat).cuda())
     assert plan.device_status() == 0
@@ -136,8 +137,8 @@ def test_morphing_enkf_chain_matches_oracle():
     abi.fftenkf_morph_inverse(ext_ref, ur, ua_ref, M, 1, ny, nx)
     torch.cuda.synchronize()
 
-    e_or = np.concatenate([T.astype(np.float64), morph.morph_forward(u, u_ref, T, 20)])
-    d_or = np.concatenate([T0.astype(np.float64), morph.morph_forward(d, u_ref[:1], T0, 20)])[:, 0]
+    e_or = np.concatenate([T.astype(np.float64), morph.morph_forward(u, u_ref, T, 20, 1e-5)])
+    d_or = np.concatenate([T0.astype(np.float64), morph.morph_forward(d, u_ref[:1], T0, 20, 1e-5)])[:, 0]
     e_or = enkf.analyze(e_or, d_or, pert, rhat, observed)
     want = morph.morph_inverse(e_or, u_ref)
     want_ref = morph.morph_inverse(morph.morph_reference(e_or), u_ref)
@@ -147,7 +148,7 @@ def test_morphing_enkf_chain_matches_oracle():
 
 def test_full_size_sampled_nodes():
     # 4096^2, M = 4, K = 20 (the bench's morphing workload): oracle at 2000 sampled (member, node).
-    M, K, ny, nx, n_iter = 4, 20, 4096, 4096, 20
+    M, K, ny, nx, n_iter, tol = 4, 20, 4096, 4096, 20, 1e-5
     g = torch.Generator(device="cuda").manual_seed(9)
     # smooth fields at full size from a coarse seeded grid, upsampled on the device (inputs only)
     coarse_u = fields.smooth_members(41, M, K, 128, 128, ell=6.0)
@@ -158,7 +159,7 @@ def test_full_size_sampled_nodes():
     u_ref = u[:, 0].clone() + 0.1 * torch.randn((M, ny, nx), generator=g, device="cuda")
     ext = torch.empty((M + 2, K, ny, nx), dtype=torch.float32, device="cuda")
     ext[:2] = T
-    _abi().fftenkf_morph_forward(u, u_ref, ext, M, K, ny, nx, n_iter)
+    _abi().fftenkf_morph_forward(u, u_ref, ext, M, K, ny, nx, n_iter, tol)
     out = torch.empty((M, K, ny, nx), dtype=torch.float32, device="cuda")
     _abi().fftenkf_morph_inverse(ext, u_ref, out, M, K, ny, nx)
     torch.cuda.synchronize()
@@ -169,7 +170,7 @@ def test_full_size_sampled_nodes():
     for k in np.unique(ks):
         sel = ks == k
         Tk = T[:, k].cpu().numpy().astype(np.float64)
-        qy, qx = morph.inverse_points_at(Tk, ys[sel], xs[sel], n_iter)
+        qy, qx = morph.inverse_points_at(Tk, ys[sel], xs[sel], n_iter, tol)
         ek = ext[:, k].cpu().numpy().astype(np.float64)
         for j in range(M):
             uj = u[j, k].cpu().numpy().astype(np.float64)
@@ -192,6 +193,8 @@ def test_rejects_bad_arguments():
     assert e.value.status == abi.FFTENKF_EINVAL
     with pytest.raises(abi.FftEnkfError):
         abi.fftenkf_morph_forward(x[:1], y, x, 1, 2, 8, 8, 2000)
+    with pytest.raises(abi.FftEnkfError):
+        abi.fftenkf_morph_forward(x[:1], y, x, 1, 2, 8, 8, 4, -1.0)
     with pytest.raises(abi.FftEnkfError):
         abi.fftenkf_morph_inverse(x, y, x, 1, 2, 8, 8)
     with pytest.raises(abi.FftEnkfError):

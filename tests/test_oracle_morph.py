@@ -116,3 +116,21 @@ def test_reference_is_member_mean():
     ext = rng.standard_normal((5, 3, 4, 6))
     np.testing.assert_allclose(morph.morph_reference(ext)[:, 0], (ext[:, 0] + ext[:, 1] + ext[:, 2]) / 3,
                                rtol=0, atol=1e-15)
+
+
+def test_tolerance_stop():
+    # tol beyond any step: every point stops after the first step, as with n_iter = 1; a small tol
+    # still solves the defining equation closely.
+    ndimage = pytest.importorskip("scipy.ndimage")
+    ny, nx = 32, 40
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((1, 2, ny, nx))
+    u_ref = rng.standard_normal((1, ny, nx))
+    T = fields.smooth_mappings(13, 2, ny, nx, amp=2.0, ell=8.0).astype(np.float64)
+    np.testing.assert_array_equal(morph.morph_forward(u, u_ref, T, 20, tol=1e9), morph.morph_forward(u, u_ref, T, 1))
+    np.testing.assert_array_equal(morph.morph_forward(u, u_ref, T, 20, tol=0.0), morph.morph_forward(u, u_ref, T, 20))
+    qy, qx = morph.inverse_points(T[:, 0], 60, tol=1e-9)
+    ty = ndimage.map_coordinates(T[1, 0], [qy, qx], order=1, mode="grid-wrap")
+    tx = ndimage.map_coordinates(T[0, 0], [qy, qx], order=1, mode="grid-wrap")
+    py, px = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    assert np.abs(qy + ty - py).max() < 1e-8 and np.abs(qx + tx - px).max() < 1e-8
