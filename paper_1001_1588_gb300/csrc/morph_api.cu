@@ -146,9 +146,13 @@ __global__ void __launch_bounds__(kThreads, 4) morph_inverse_kernel(const float*
   }
 }
 
-// Launch shape of the per-member kernels: member k on grid.y, about kGrid CTAs in all.
+// Launch shape of the per-member kernels: member k on grid.y and floor(kResident / K) CTAs per member,
+// so that every CTA is resident at once (one wave, no tail of a few CTAs each looping over its whole
+// share of the plane).  kResident = 152 SMs x 4 CTAs of 256 threads at 64 registers (the cap that
+// __launch_bounds__(kThreads, 4) sets).
+constexpr int kResident = 152 * 4;
 dim3 member_grid(int plane, int K) {
-  int gx = (kGrid + K - 1) / K;
+  int gx = kResident / K;
   const int need = (plane + kThreads - 1) / kThreads;
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
