@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) morph_reference_kernel(const float* 
 
 // grid (x: nodes of one plane, grid-stride; y: member k): u_out[j][k](p) = (u_ref[j] + r[j][k]) at
 // p + T_k(p).
-__global__ void __launch_bounds__(kThreads, 4) morph_inverse_kernel(const float* __restrict__ ext,
+__global__ void __launch_bounds__(kThreads, 8) morph_inverse_kernel(const float* __restrict__ ext,
                                                                  const float* __restrict__ u_ref,
                                                                  float* __restrict__ u_out, int M, int K, int ny,
                                                                  int nx) {
@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kThreads, 4) morph_inverse_kernel(const float*
   for (int p = blockIdx.x * kThreads + threadIdx.x; p < plane; p += gridDim.x * kThreads) {
     const int y = p / nx, x = p - y * nx;
     const Stencil s = stencil(y, x, __ldg(ty + p), __ldg(tx + p), ny, nx);
+#pragma unroll 1   // 31 registers: 8 CTAs (2048 threads) per SM keep more gathers in flight
     for (int j = 0; j < M; ++j) {
       const float* g = u_ref + (size_t)j * plane;
       const float* r = ext + ((size_t)(2 + j) * K + k) * plane;
@@ -146,13 +147,14 @@ __global__ void __launch_bounds__(kThreads, 4) morph_inverse_kernel(const float*
   }
 }
 
-// Launch shape of the per-member kernels: member k on grid.y and floor(kResident / K) CTAs per member,
+// Launch shape of the per-member kernels: member k on grid.y and floor(resident / K) CTAs per member,
 // so that every CTA is resident at once (one wave, no tail of a few CTAs each looping over its whole
-// share of the plane).  kResident = 152 SMs x 4 CTAs of 256 threads at 64 registers (the cap that
-// __launch_bounds__(kThreads, 4) sets).
-constexpr int kResident = 152 * 4;
-dim3 member_grid(int plane, int K) {
-  int gx = kResident / K;
+// share of the plane).  resident = 152 SMs x the CTAs of 256 threads that fit per SM under the
+// kernel's __launch_bounds__: 4 for the forward (64 registers), 8 for the inverse (32 registers).
+constexpr int kResidentForward = 152 * 4;
+constexpr int kResidentInverse = 152 * 8;
+dim3 member_grid(int plane, int K, int resident) {
+  int gx = resident / K;
   const int need = (plane + kThreads - 1) / kThreads;
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
@@ -204,7 +206,7 @@ extern "C" fftenkf_status fftenkf_morph_forward(const float* u, const float* u_r
   if (overlaps(r, r_bytes, u, r_bytes) || overlaps(r, r_bytes, u_ref, (size_t)n_blocks * plane) ||
       overlaps(r, r_bytes, ext, (size_t)2 * n_members * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": the residual blocks of ext overlap an input");
-  morph_forward_kernel<<<member_grid(ny * nx, n_members), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_forward_kernel<<<member_grid(ny * nx, n_members, kResidentForward), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter, tol);
   return finish(who);
 }
@@ -237,7 +239,7 @@ extern "C" fftenkf_status fftenkf_morph_inverse(const float* ext, const float* u
   if (overlaps(u_out, out_bytes, ext, (size_t)(n_blocks + 2) * n_members * plane) ||
       overlaps(u_out, out_bytes, u_ref, (size_t)n_blocks * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": u_out overlaps an input");
-  morph_inverse_kernel<<<member_grid(ny * nx, n_members), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_inverse_kernel<<<member_grid(ny * nx, n_members, kResidentInverse), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       ext, u_ref, u_out, n_blocks, n_members, ny, nx);
   return finish(who);
 }
