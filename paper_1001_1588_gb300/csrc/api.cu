@@ -120,16 +120,10 @@ static void host_twiddles(std::vector<float2>& out, int n, int count) {
   for (int e = 0; e < count; ++e) out.push_back(unit_root(e, n));
 }
 
-// stage-major table of the line FFT plan (n, default V), laid out as fft_core.cuh reads it
+// stage-major table of the line FFT plan (n, V), laid out as fft_core.cuh reads it
 static void host_stage_twiddles(std::vector<float2>& out, int n, int V) {
-  const int S = num_stages(n, V);
-  const size_t base = out.size();
-  for (int s = 1; s < S; ++s) {
-    const int R = radix_at(n, V, s), NS = stage_ns(n, V, s);
-    for (int r = 1; r < R; ++r)
-      for (int jm = 0; jm < NS; ++jm) out.push_back(unit_root((long long)jm * r * (n / (NS * R)), n));
-  }
-  if (out.size() - base != (size_t)twiddle_count(n, V)) out.resize(base + twiddle_count(n, V));
+  const int count = twiddle_count(n, V);
+  for (int i = 0; i < count; ++i) out.push_back(unit_root(twiddle_exponent(n, V, i), n));
 }
 
 // covariance tables per wavenumber in the column statistics

@@ -138,15 +138,9 @@ extern "C" fftenkf_status fftenkf_plan_batched(fftenkf_batch* out, int count, co
     if (off_stage[sel].count(n)) return;
     off_stage[sel][n] = tw.size();
     const int V = plan_V(n, sel);
-    const int S = num_stages(n, V);
-    for (int s = 1; s < S; ++s) {
-      const int R = radix_at(n, V, s), NS = stage_ns(n, V, s);
-      for (int r = 1; r < R; ++r)
-        for (int jm = 0; jm < NS; ++jm) {
-          const long long e = (long long)jm * r * (n / (NS * R)) % n;
-          const double ang = 2.0 * M_PI * (double)e / (double)n;
-          tw.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
-        }
+    for (int i = 0; i < twiddle_count(n, V); ++i) {
+      const double ang = 2.0 * M_PI * (double)twiddle_exponent(n, V, i) / (double)n;
+      tw.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
     }
     if (tw.size() % 2) tw.push_back(make_float2(0.f, 0.f));
   };

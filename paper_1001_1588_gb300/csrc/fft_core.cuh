@@ -186,10 +186,16 @@ template <bool INV> struct Dft<16, INV> {
   }
 };
 
-// Twiddle tables: for every stage s with NS > 1 the factors
-// W_N^((j mod NS) r N/(NS R)) are stored as rows r = 1..R-1 of NS entries, so
-// the threads of a warp (consecutive j) read consecutive entries.  Stages are
+// Twiddle tables.  Butterfly j of a stage with NS > 1 multiplies its input r by w^r,
+// w = W_N^((j mod NS) N/(NS R)).  The table stores only the powers w^p for p in
+// {1, 2, 4, 8} below R (w and w^2 for radix 3), as rows of NS entries (the threads of a
+// warp, consecutive j, read consecutive entries); the butterfly forms the other powers
+// by at most three complex products (w^3 = w^2 w, w^5 = w^4 w, ..., w^15 = w^8 w^7).
+// A 4096-point plan then needs 1088 entries (8.5 KB) instead of 4080, which stay in L1
+// when a pass gives most of the SM's on-chip memory to shared memory.  Stages are
 // concatenated in order; twiddle_offset(N, V, s) is where stage s starts.
+__host__ __device__ constexpr int tw_npow(int R) { return R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : R == 3 ? 2 : 1; }
+__host__ __device__ constexpr int tw_pow(int q) { return 1 << q; }   // the q-th stored power
 __host__ __device__ constexpr int stage_ns(int N, int V, int s) {
   int ns = 1;
   for (int i = 0; i < s; ++i) ns *= radix_at(N, V, i);
@@ -197,10 +203,38 @@ __host__ __device__ constexpr int stage_ns(int N, int V, int s) {
 }
 __host__ __device__ constexpr int twiddle_offset(int N, int V, int s) {
   int off = 0;
-  for (int i = 1; i < s; ++i) off += (radix_at(N, V, i) - 1) * stage_ns(N, V, i);
+  for (int i = 1; i < s; ++i) off += tw_npow(radix_at(N, V, i)) * stage_ns(N, V, i);
   return off;
 }
 __host__ __device__ constexpr int twiddle_count(int N, int V) { return twiddle_offset(N, V, num_stages(N, V)); }
+// exponent e (of W_N^e = exp(-2 pi i e / N)) of table entry i, 0 <= i < twiddle_count(N, V)
+__host__ __device__ constexpr long long twiddle_exponent(int N, int V, int i) {
+  const int S = num_stages(N, V);
+  int s = 1;
+  while (s + 1 < S && twiddle_offset(N, V, s + 1) <= i) ++s;
+  const int NS = stage_ns(N, V, s), R = radix_at(N, V, s);
+  const int local = i - twiddle_offset(N, V, s);
+  const int q = local / NS, jm = local - q * NS;
+  return ((long long)jm * tw_pow(q) * (N / (NS * R))) % N;
+}
+
+// w^r for r = 1..R-1 of one butterfly from the stored powers (tws: this butterfly's
+// first entry; rows NS apart); conjugated for the inverse transform
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle_powers(float2 (&w)[R], const float2* __restrict__ tws, int NS) {
+#pragma unroll
+  for (int q = 0; q < tw_npow(R); ++q) {
+    float2 x = __ldg(tws + q * NS);
+    if (INV) x.y = -x.y;
+    w[tw_pow(q)] = x;
+  }
+#pragma unroll
+  for (int r = 3; r < R; ++r) {
+    if ((r & (r - 1)) == 0) continue;          // stored
+    const int hi = r >= 8 ? 8 : (r >= 4 ? 4 : 2);   // largest stored power below r
+    w[r] = cmul(w[hi], w[r - hi]);
+  }
+}
 
 // Barrier over the threads that transform one line: the whole CTA (bid 0) or
 // named barrier bid over the line's T threads, when each line owns whole warps
@@ -240,13 +274,10 @@ struct Stage {
       for (int r = 0; r < R; ++r) a[r] = v[b + r * B];
       const int j = t + T * b;
       if (NS > 1) {
-        const float2* tws = tw + twiddle_offset(N, V, S) + (j % NS);
+        float2 w[R];
+        twiddle_powers<R, INV>(w, tw + twiddle_offset(N, V, S) + (j % NS), NS);
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(tws + (r - 1) * NS);
-          if (INV) w.y = -w.y;
-          a[r] = cmul(a[r], w);
-        }
+        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[r]);
       }
       Dft<R, INV>::run(a);
       if (LAST) {

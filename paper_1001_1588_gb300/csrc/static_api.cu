@@ -36,15 +36,9 @@ size_t rup(size_t x) { return (x + 255) / 256 * 256; }
 
 // stage-major twiddles of the (N, V) line plan, computed on the device (see fft_core.cuh)
 __global__ void stage_twiddles_kernel(float2* out, int N, int V) {
-  const int S = num_stages(N, V);
-  const int count = twiddle_offset(N, V, S);
+  const int count = twiddle_count(N, V);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    int s = 1;
-    while (s + 1 < S && twiddle_offset(N, V, s + 1) <= i) ++s;
-    const int NS = stage_ns(N, V, s), R = radix_at(N, V, s);
-    const int local = i - twiddle_offset(N, V, s);
-    const int r = local / NS + 1, jm = local - (local / NS) * NS;
-    const long long e = ((long long)jm * r * (N / (NS * R))) % N;
+    const long long e = twiddle_exponent(N, V, i);
     double sn, cs;
     sincospi(2.0 * (double)e / (double)N, &sn, &cs);
     out[i] = make_float2((float)cs, (float)-sn);
