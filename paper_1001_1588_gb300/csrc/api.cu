@@ -11,6 +11,10 @@
 //   7. row_inv         inverse rows, u_k^(j) += increment
 // With a caller-supplied spectrum, 1-3 are skipped and the gain pass (4) reads the
 // tables on the auxiliary stream, overlapping 5.
+// When the fused column pass covers the plan (one or two observed blocks, not coupled, the
+// wide column schedule), steps 3 and 6 are one launch after step 5:
+//   5. row_fwd innov, 3+6. col_fused (columns of F, chat, gains, gain x innovation, inverse
+//   columns -> S), 7. row_inv.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,10 +28,10 @@
 using namespace fftenkf;
 
 enum Pass { kPassMean, kPassRowAnom, kPassStats, kPassGain, kPassRowInnov, kPassUpdate, kPassRowInv,
-            kPassChatOut, kPassRhatT, kPassCount };
+            kPassChatOut, kPassRhatT, kPassFused, kPassCount };
 static const char* kPassNames[kPassCount] = {"mean", "row_fwd_anomaly", "col_stats", "gain",
                                              "row_fwd_innovation", "col_update", "row_inv", "chat_out",
-                                             "rhat_transpose"};
+                                             "rhat_transpose", "col_fused"};
 
 namespace {
 thread_local std::string g_last_error;
@@ -56,6 +60,9 @@ struct fftenkf_plan_s {
   int obs_of_block[kMaxBlocks];
   int un_of_block[kMaxBlocks];
   float2* d_tw = nullptr;     // [L] row twiddles, [ny] column twiddles, [L+1] real-FFT twiddles
+  float4* d_tw4 = nullptr;    // paired column twiddles of the fused column pass, both schedules
+  size_t off_tw4[2] = {0, 0};
+  bool fused_ok[2] = {false, false};   // the fused column pass covers the plan with schedule 0 / 1
   int* d_status = nullptr;
   cudaStream_t aux = nullptr;
   bool coupled = false;   // observed blocks coupled through their cross-covariance (n_obs <= 2)
@@ -82,6 +89,10 @@ struct fftenkf_plan_s {
   const float2* twL(int sel) const { return d_tw + off_twL[sel]; }
   const float2* twY(int sel) const { return d_tw + off_twY[sel]; }
   const float2* twX() const { return d_tw + off_twX; }
+  // the fused column pass runs when it covers the plan and the column schedules are the wide ones
+  bool use_fused() const {
+    return fused_ok[sched[kPassFused] & 1] && !coupled && sched[kPassStats] == 0 && sched[kPassUpdate] == 0;
+  }
 };
 
 // fold a completed slot into the totals
@@ -206,6 +217,20 @@ extern "C" fftenkf_status fftenkf_plan_create(fftenkf_plan* plan, const fftenkf_
     return fail(FFTENKF_ENOMEM, "twiddle allocation failed");
   }
   e = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  std::vector<float4> t4;
+  for (int sel = 0; sel < 2; ++sel) {
+    p->fused_ok[sel] = col_fused_supported(p->ny, p->n_obs, p->M, sel);
+    if (!p->fused_ok[sel]) continue;
+    std::vector<float2> t1;
+    host_stage_twiddles(t1, p->ny, plan_V(p->ny, sel));
+    p->off_tw4[sel] = t4.size();
+    for (const float2& w : t1) t4.push_back(make_float4(w.x, w.x, w.y, w.y));
+    t4.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+  }
+  if (e == cudaSuccess && !t4.empty()) {
+    e = cudaMalloc(&p->d_tw4, t4.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw4, t4.data(), t4.size() * sizeof(float4), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
@@ -223,6 +248,7 @@ extern "C" fftenkf_status fftenkf_plan_destroy(fftenkf_plan p) {
   if (!p) return FFTENKF_OK;
   if (p->own_ws) cudaFree(p->own_ws);
   if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_tw4) cudaFree(p->d_tw4);
   if (p->d_status) cudaFree(p->d_status);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
@@ -264,6 +290,21 @@ static fftenkf_status get_workspace(fftenkf_plan p, void* ws, char** out) {
   }
   *out = static_cast<char*>(p->own_ws);
   return FFTENKF_OK;
+}
+
+static ColFusedParams fused_params(fftenkf_plan p, char* ws) {
+  ColFusedParams f;
+  memset(&f, 0, sizeof(f));
+  f.ny = p->ny; f.L = p->L; f.M = p->M; f.N = p->N; f.n_obs = p->n_obs; f.n_un = p->n_un;
+  for (int r = 0; r < p->M; ++r) f.role_block[r] = (r < p->n_obs) ? p->obs[r] : p->un[r - p->n_obs];
+  f.A = reinterpret_cast<const float2*>(ws + p->off_A);
+  f.S = reinterpret_cast<float2*>(ws + p->off_A);
+  f.vsel = p->sched[kPassFused] & 1;
+  f.tw = p->d_tw4 + p->off_tw4[f.vsel];
+  f.scale = (float)(1.0 / ((double)(p->N - 1) * (double)p->ny * (double)p->nx));
+  f.inv_G = (float)(1.0 / ((double)p->ny * (double)p->nx));
+  f.status = p->d_status;
+  return f;
 }
 
 // steps 1-3: mean, anomaly row spectra, column statistics -> chat_t
@@ -315,9 +356,46 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
     e = cudaStreamWaitEvent(s, wait_before_stats, 0);
     if (e != cudaSuccess) return e;
   }
+  if (!rhat_t && p->use_fused()) {   // statistics only: the fused column pass writes the tables
+    ColFusedParams f = fused_params(p, ws);
+    f.chat = cp.chat;
+    prof_begin(p, kPassFused, s);
+    e = launch_col_fused(f, s);
+    prof_end(p, kPassFused, s);
+    return e;
+  }
   prof_begin(p, kPassStats, s);
   e = launch_col_stats(cp, s);
   prof_end(p, kPassStats, s);
+  return e;
+}
+
+// steps 1-2 only (the fused path transforms the columns later)
+static cudaError_t run_mean_rows(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s) {
+  MeanParams mp;
+  mp.M = p->M;
+  mp.N = p->N;
+  mp.storage = p->storage;
+  mp.G = (long long)p->ny * p->nx;
+  mp.ens = ens;
+  mp.mean = reinterpret_cast<float*>(ws + p->off_mean);
+  mp.status = p->d_status;
+  mp.vsel = p->sched[kPassMean];
+  prof_begin(p, kPassMean, s);
+  cudaError_t e = launch_mean(mp, s);
+  prof_end(p, kPassMean, s);
+  if (e != cudaSuccess) return e;
+  RowFwdParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
+  rp.n_obs = p->n_obs; rp.mode = kAnomaly; rp.storage = p->storage;
+  rp.ens = ens; rp.mean = mp.mean;
+  rp.out = reinterpret_cast<float2*>(ws + p->off_A);
+  rp.vsel = p->sched[kPassRowAnom];
+  rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
+  prof_begin(p, kPassRowAnom, s);
+  e = launch_row_fwd(rp, p->M * p->N, s);
+  prof_end(p, kPassRowAnom, s);
   return e;
 }
 
@@ -388,7 +466,11 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
     prof_end(p, kPassGain, p->aux);
   }
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
-  if (!spectrum && p->coupled) {
+  const bool fused = !spectrum && !drawn && p->use_fused();
+  if (fused) {
+    // mean and anomaly rows now; the columns after the innovation rows
+    if (e == cudaSuccess) e = run_mean_rows(p, ensemble, ws, s);
+  } else if (!spectrum && p->coupled) {
     // tables of the column statistics, then the coupled gains (FP64 bracket inverse per wavenumber)
     if (e == cudaSuccess) e = run_statistics(p, ensemble, ws, s, nullptr);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
@@ -438,9 +520,19 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
   up.S = reinterpret_cast<float2*>(ws + p->off_A);
   up.vsel = p->sched[kPassUpdate];
   up.twY = p->twY(up.vsel); up.status = p->d_status;
-  prof_begin(p, kPassUpdate, s);
-  if (e == cudaSuccess) e = launch_col_update(up, s);
-  prof_end(p, kPassUpdate, s);
+  if (fused) {
+    ColFusedParams f = fused_params(p, ws);
+    f.W = rp.out;
+    f.rhat_t = rhat_t;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+    prof_begin(p, kPassFused, s);
+    if (e == cudaSuccess) e = launch_col_fused(f, s);
+    prof_end(p, kPassFused, s);
+  } else {
+    prof_begin(p, kPassUpdate, s);
+    if (e == cudaSuccess) e = launch_col_update(up, s);
+    prof_end(p, kPassUpdate, s);
+  }
   RowInvParams ip;
   memset(&ip, 0, sizeof(ip));
   ip.ny = p->ny; ip.nx = p->nx; ip.L = p->L; ip.M = p->M; ip.N = p->N; ip.storage = p->storage;

@@ -171,6 +171,28 @@ struct ColUpdParams {
   float sqrt_G;
 };
 
+// Fused column pass (statistics, gains and update of one wavenumber column per thread group,
+// per-column tables in tensor memory): one or two observed blocks, not coupled.  Blocks are
+// taken in "role" order, observed first, and transformed two at a time.
+struct ColFusedParams {
+  int ny, L, M, N, n_obs, n_un;
+  int role_block[kMaxBlocks];   // block of role r (r < n_obs: the observed ones)
+  const float2* A;        // anomaly row spectra, field j*N+k
+  const float2* W;        // innovation row spectra, field k*n_obs+i; null: statistics only
+  float2* S;              // increment row spectra, field j*N+k (may alias A)
+  const double* rhat_t;   // [n_obs][L+1][ny] (analysis)
+  float* chat;            // statistics only: tables in the col_stats layout
+  const float4* tw;       // paired compact stage twiddles of the ny-point plan
+  float scale;            // 1 / ((N-1) ny nx)
+  float inv_G;            // 1 / (ny nx)
+  int* status;
+  int vsel;               // line-FFT schedule: 0 = wide (V = 16), 1 = narrow (V = 8, twice the threads)
+};
+// launch of the fused column pass; cudaErrorNotSupported when the shape is not covered
+cudaError_t launch_col_fused(const ColFusedParams& p, cudaStream_t s);
+// whether the fused column pass covers (ny, n_obs, blocks) with schedule sel
+bool col_fused_supported(int ny, int n_obs, int M, int sel);
+
 struct GainParams {
   int ny, L, n_obs, n_un;
   const float* chat_t;    // stats kernel output (transposed, float), or null

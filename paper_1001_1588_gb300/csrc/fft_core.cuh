@@ -239,10 +239,13 @@ __device__ __forceinline__ void twiddle_powers(float2 (&w)[R], const float2* __r
 // Barrier over the threads that transform one line: the whole CTA (bid 0) or
 // named barrier bid over the line's T threads, when each line owns whole warps
 // and the CTA holds several lines, so that lines progress independently.
+// bid < 0: the line is one warp, which synchronises alone.
 template <int T>
 __device__ __forceinline__ void line_sync(int bid) {
   if (bid == 0) {
     __syncthreads();
+  } else if (bid < 0) {
+    __syncwarp();
   } else {
     asm volatile("bar.sync %0, %1;" ::"r"(bid), "n"(T) : "memory");
   }

@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "k_cols.cuh"
+#include "k_colf.cuh"
 
 namespace fftenkf {
 
@@ -86,6 +87,27 @@ cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s) {
   if (p.n_obs <= 1) return col_update_nobs1(p, s);
   if (p.n_obs <= 2) return col_update_nobs2(p, s);
   return col_update_nobs4(p, s);
+}
+
+bool col_fused_supported(int ny, int n_obs, int M, int sel) {
+  switch (ny) {
+#define CASE(n) case n:
+    FFTENKF_FUSED_SIZES(CASE)
+#undef CASE
+      break;
+    default:
+      return false;
+  }
+  if (n_obs < 1 || n_obs > 2 || M < n_obs) return false;
+  const ColFusedLaunch s = col_fused_launch(ny, sel);
+  if (s.lpc < 1) return false;
+  const int nf = n_obs * (1 + 2 * (M - n_obs));   // sums / gains per wavenumber
+  return (nf + 4) * s.V <= s.cols_per_thread;     // + the member's spectra (two complex halves)
+}
+
+cudaError_t launch_col_fused(const ColFusedParams& p, cudaStream_t s) {
+  if (!col_fused_supported(p.ny, p.n_obs, p.M, p.vsel)) return cudaErrorNotSupported;
+  return p.n_obs == 1 ? col_fused_nobs1(p, s) : col_fused_nobs2(p, s);
 }
 
 bool line_supported(int n) {

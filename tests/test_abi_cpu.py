@@ -58,8 +58,9 @@ def test_status_strings(lib):
     from paper_1001_1588_gb300 import abi
     assert abi.fftenkf_status_string(0) == "ok"
     assert "invalid" in abi.fftenkf_status_string(1)
-    assert abi.fftenkf_pass_count() == 9
+    assert abi.fftenkf_pass_count() == 10
     assert abi.fftenkf_pass_name(2) == "col_stats"
+    assert abi.fftenkf_pass_name(9) == "col_fused"
 
 
 def test_missing_library_fails_loudly(monkeypatch):
