@@ -52,7 +52,7 @@ typedef enum {
   FFTENKF_EUNSUPPORTED = 2,  /* size not 2^a or 3*2^a in range, N < 2, too many blocks */
   FFTENKF_ECUDA = 3,         /* a CUDA runtime call failed */
   FFTENKF_ENONFINITE = 4,    /* non-finite spectral covariance seen on the device */
-  FFTENKF_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+  FFTENKF_ETIMEOUT = 5,      /* a bounded device wait for an asynchronous copy gave up */
   FFTENKF_ENOMEM = 6         /* device allocation failed */
 } fftenkf_status;
 
@@ -135,7 +135,8 @@ fftenkf_status fftenkf_analyze_seeded(fftenkf_plan plan, void* ensemble, const f
  * loading this library holds until the process exits.  It allocates nothing
  * and calls no allocating routine.
  *   ensemble      [N][ny][nx] device array of the storage type (one block)
- *   spectrum_out  [ny][nx/2+1] device doubles: chat of eq. (dii), unitary scaling
+ *   spectrum_out  [ny][nx/2+1] device doubles: the same single-block table that
+ *                 fftenkf_estimate_spectrum writes (unitary scaling)
  * Sizes follow the plan limits; a problem whose scratch exceeds the array
  * (about N (nx/2) ny 8 + ny nx 4 bytes plus small tables > 64 MiB) returns
  * FFTENKF_EUNSUPPORTED with a message giving the bytes needed.  The first call
@@ -144,14 +145,34 @@ fftenkf_status fftenkf_analyze_seeded(fftenkf_plan plan, void* ensemble, const f
  * stream capture.  All calls share the one array and it keeps the last call's
  * contents; calls that overlap on the GPU (on different streams, or from
  * different host threads) race on it and must be serialised by the caller.
- * Non-finite covariance values appear in spectrum_out as such. */
+ * Each call clears the array's status word before its kernels run; whether a
+ * bounded wait gave up (the table then holds stale values) or a covariance value
+ * was not finite is read with fftenkf_static_last_device_status. */
 fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble, int ny, int nx, int n_members, int storage,
                                                 double* spectrum_out, void* stream);
 
+/* Status of the last fftenkf_estimate_spectrum_static calls on the current
+ * device (the paper has no counterpart): waits for `stream`, reads and clears the
+ * static array's status word without allocating, and returns FFTENKF_OK,
+ * FFTENKF_ETIMEOUT (a bounded wait for a copy gave up: spectrum_out is stale),
+ * FFTENKF_ENONFINITE (a covariance value was not finite), or FFTENKF_ECUDA if the
+ * stream reported an error.  Reads before any call on the device return OK. */
+fftenkf_status fftenkf_static_last_device_status(void* stream);
+
 /* Wait for `stream`, then return and clear the plan's device status word:
- * FFTENKF_OK, FFTENKF_ENONFINITE, or FFTENKF_ECUDA if the stream reported an
- * error. */
+ * FFTENKF_OK, FFTENKF_ETIMEOUT (a bounded wait for an asynchronous copy gave up;
+ * the outputs of that call are incomplete), FFTENKF_ENONFINITE, or FFTENKF_ECUDA
+ * if the stream reported an error. */
 fftenkf_status fftenkf_last_device_status(fftenkf_plan plan, void* stream);
+
+/* Test setting of the error path of the bounded waits: with on != 0, every CTA
+ * of the forward anomaly row pass gives up its first wait for a bulk copy at
+ * once, as a wait that ran out of time does -- it records the timeout, lets
+ * its copies in flight land (a wait bounded at 2 s) and leaves -- so the calls
+ * made meanwhile report FFTENKF_ETIMEOUT through fftenkf_last_device_status
+ * and their outputs are incomplete.  No kernel faults or hangs.  Off (0) by
+ * default; set it back to 0 to compute again. */
+fftenkf_status fftenkf_set_expire_first_wait(fftenkf_plan plan, int on);
 
 /* Per-pass timing (tracing).  With profiling enabled every pass of the calls
  * on this plan is bracketed by CUDA events on the stream it runs on.

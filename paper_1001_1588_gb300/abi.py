@@ -47,6 +47,7 @@ _SIGNATURES = [
     ("fftenkf_analyze_seeded", ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_ulonglong] + [ctypes.c_void_p] * 2),
     ("fftenkf_estimate_spectrum_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fftenkf_static_last_device_status", ctypes.c_int, [ctypes.c_void_p]),
     ("fftenkf_last_device_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("fftenkf_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("fftenkf_pass_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -55,6 +56,7 @@ _SIGNATURES = [
     ("fftenkf_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("fftenkf_set_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("fftenkf_set_expire_first_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("fftenkf_pass_name", ctypes.c_char_p, [ctypes.c_int]),
     ("fftenkf_plan_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(fftenkf_dims)]),
     ("fftenkf_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
@@ -180,6 +182,11 @@ def fftenkf_estimate_spectrum_static(ensemble, ny, nx, n_members, storage, spect
           "fftenkf_estimate_spectrum_static")
 
 
+def fftenkf_static_last_device_status(stream=None) -> int:
+    """Status word of the allocation-free calls on the current device (waits for the stream, clears it)."""
+    return lib().fftenkf_static_last_device_status(stream)
+
+
 def fftenkf_sine_plan_create(ny, nx, n_blocks, n_members, storage, observed_mask):
     d = fftenkf_dims(ny, nx, n_blocks, n_members, storage)
     plan = ctypes.c_void_p()
@@ -259,6 +266,11 @@ def fftenkf_set_schedule(plan, sched):
 
 def fftenkf_set_coupled(plan, coupled):
     check(lib().fftenkf_set_coupled(plan, int(bool(coupled))), "fftenkf_set_coupled")
+
+
+def fftenkf_set_expire_first_wait(plan, on):
+    """Test setting: every CTA of the forward anomaly row pass gives up its first bulk-copy wait."""
+    check(lib().fftenkf_set_expire_first_wait(plan, int(bool(on))), "fftenkf_set_expire_first_wait")
 
 
 def fftenkf_get_schedule(plan):

@@ -86,6 +86,7 @@ struct fftenkf_plan_s {
   int launches[kPassCount] = {};
   size_t off_twL[2] = {0, 0}, off_twY[2] = {0, 0}, off_twX = 0;
   int sched[kPassCount] = {};   // line-FFT schedule (plan_V selector) per pass
+  int expire_first_wait = 0;    // test setting (fftenkf_set_expire_first_wait)
   const float2* twL(int sel) const { return d_tw + off_twL[sel]; }
   const float2* twY(int sel) const { return d_tw + off_twY[sel]; }
   const float2* twX() const { return d_tw + off_twX; }
@@ -332,6 +333,7 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   rp.out = reinterpret_cast<float2*>(ws + p->off_A);
   rp.vsel = p->sched[kPassRowAnom];
   rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
+  rp.expire_first_wait = p->expire_first_wait;
   prof_begin(p, kPassRowAnom, s);
   e = launch_row_fwd(rp, p->M * p->N, s);
   prof_end(p, kPassRowAnom, s);
@@ -393,6 +395,7 @@ static cudaError_t run_mean_rows(fftenkf_plan p, const void* ens, char* ws, cuda
   rp.out = reinterpret_cast<float2*>(ws + p->off_A);
   rp.vsel = p->sched[kPassRowAnom];
   rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
+  rp.expire_first_wait = p->expire_first_wait;
   prof_begin(p, kPassRowAnom, s);
   e = launch_row_fwd(rp, p->M * p->N, s);
   prof_end(p, kPassRowAnom, s);
@@ -667,6 +670,12 @@ extern "C" fftenkf_status fftenkf_set_coupled(fftenkf_plan p, int coupled) {
     p->own_ws = nullptr;
   }
   p->tm_S = nullptr;   // the tensor map is encoded again for the new layout
+  return FFTENKF_OK;
+}
+
+extern "C" fftenkf_status fftenkf_set_expire_first_wait(fftenkf_plan p, int on) {
+  if (!p) return fail(FFTENKF_EINVAL, "null argument");
+  p->expire_first_wait = on ? 1 : 0;
   return FFTENKF_OK;
 }
 

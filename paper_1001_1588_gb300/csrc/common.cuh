@@ -101,6 +101,7 @@ struct RowFwdParams {
   const float2* twX;      // exp(-2 pi i k / nx), k <= L
   int* status;
   int vsel;               // line-FFT schedule (plan_V)
+  int expire_first_wait;  // test setting: every CTA's first bulk-copy wait gives up at once
 };
 
 struct RowInvParams {

@@ -54,12 +54,6 @@ __device__ __forceinline__ cp cp_rot(cp d) {
   const float2 z = make_float2(0.f, 0.f);
   return INV ? cp{p_sub(z, d.im), d.re} : cp{d.im, p_sub(z, d.re)};
 }
-// a * w (forward) or a * conj(w) (INV) for the broadcast factor w = (wr, wi)
-template <bool INV>
-__device__ __forceinline__ cp cp_twiddle(cp a, float2 wr, float2 wi) {
-  if (INV) return {p_fma(a.im, wi, p_mul(a.re, wr)), p_sub(p_mul(a.im, wr), p_mul(a.re, wi))};
-  return {p_sub(p_mul(a.re, wr), p_mul(a.im, wi)), p_fma(a.re, wi, p_mul(a.im, wr))};
-}
 // 16-byte shared-memory form {a.re, b.re, a.im, b.im}
 __device__ __forceinline__ float4 cp_pack(cp a) { return make_float4(a.re.x, a.re.y, a.im.x, a.im.y); }
 __device__ __forceinline__ cp cp_unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }

@@ -81,7 +81,7 @@ __device__ void batch_row_fwd_unit(const BatchItem& it, int u, int mode, int sto
       } else {
         const float2 dd = act ? *reinterpret_cast<const float2*>(it.data + idx) : make_float2(0.f, 0.f);
         const float2 ee = act ? load2(eb, idx, storage) : make_float2(0.f, 0.f);
-        v[m] = make_float2((dd.x + ee.x) - a.x, (dd.y + ee.y) - a.y);
+        v[m] = make_float2((dd.x - a.x) + ee.x, (dd.y - a.y) + ee.y);   // d - u first: exact for close d, u
       }
     }
     float2* line = sm + (act ? row : R) * pitch;     // idle groups use a spare line

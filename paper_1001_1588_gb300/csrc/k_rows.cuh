@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   const int RP = p.R >> 1;
   const int rp = threadIdx.x % RP;
   const int cstep = blockDim.x / RP;
+  bool expire = p.expire_first_wait != 0;   // test setting: the CTA's first wait gives up
   for (; q < Q; q += gridDim.x) {
     const RowTile w = decode_tile(q, p.N, p.n_tiles);
     const int y0 = w.tile * p.R;
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
       float2 sv[V];
 #pragma unroll
       for (int m = 0; m < V; ++m) sv[m] = __ldg(reinterpret_cast<const float2*>(sh) + t + T * m);
-      if (!cta_wait(bar, phase, p.status, flag)) return;
+      if (!cta_wait(bar, phase, p.status, flag, expire)) return;
+      expire = false;
       phase ^= 1;
       float2 v[V];
       const unsigned char* st_row = stage + (size_t)g * nx * es;
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
           v[m] = make_float2(a.x - sv[m].x, a.y - sv[m].y);
         } else if constexpr (MODE == kInnovation) {
           const float2 ee = load2<ST>(st_row + round_bytes, idx);
-          v[m] = make_float2((sv[m].x + ee.x) - a.x, (sv[m].y + ee.y) - a.y);
+          // w = (d - u) + e: d - u first, exact when d and u are close (large common mean)
+          v[m] = make_float2((sv[m].x - a.x) + ee.x, (sv[m].y - a.y) + ee.y);
         } else {
           v[m] = make_float2(sv[m].x - a.x, sv[m].y - a.y);
         }

@@ -27,7 +27,6 @@ void set_last_error(const std::string& msg);
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kGrid = 152 * 8;          // 8 resident CTAs on each of the 152 SMs
 constexpr float kMaxOffset = 4194304.f;  // 2^22 cells: offsets are clamped to this for indexing
 constexpr int kMaxIter = 1024;
 
@@ -149,10 +148,23 @@ __global__ void __launch_bounds__(kThreads, 8) morph_inverse_kernel(const float*
 
 // Launch shape of the per-member kernels: member k on grid.y and floor(resident / K) CTAs per member,
 // so that every CTA is resident at once (one wave, no tail of a few CTAs each looping over its whole
-// share of the plane).  resident = 152 SMs x the CTAs of 256 threads that fit per SM under the
-// kernel's __launch_bounds__: 4 for the forward (64 registers), 8 for the inverse (32 registers).
-constexpr int kResidentForward = 152 * 4;
-constexpr int kResidentInverse = 152 * 8;
+// share of the plane).  resident = the SM count x the CTAs of 256 threads that fit on one SM, as the
+// occupancy calculator gives them for the kernel (4 for the forward at 64 registers, 8 for the inverse
+// at 32 on a 152-SM GB300).
+template <typename K>
+int resident_ctas(K kernel) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return sms * per_sm;
+}
 dim3 member_grid(int plane, int K, int resident) {
   int gx = resident / K;
   const int need = (plane + kThreads - 1) / kThreads;
@@ -161,9 +173,9 @@ dim3 member_grid(int plane, int K, int resident) {
   return dim3(gx, K);
 }
 
-int grid_for(size_t units) {
+int grid_for(size_t units, int resident) {
   const size_t g = (units + kThreads - 1) / kThreads;
-  return (int)(g < (size_t)kGrid ? (g ? g : 1) : (size_t)kGrid);
+  return (int)(g < (size_t)resident ? (g ? g : 1) : (size_t)resident);
 }
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -206,7 +218,7 @@ extern "C" fftenkf_status fftenkf_morph_forward(const float* u, const float* u_r
   if (overlaps(r, r_bytes, u, r_bytes) || overlaps(r, r_bytes, u_ref, (size_t)n_blocks * plane) ||
       overlaps(r, r_bytes, ext, (size_t)2 * n_members * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": the residual blocks of ext overlap an input");
-  morph_forward_kernel<<<member_grid(ny * nx, n_members, kResidentForward), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_forward_kernel<<<member_grid(ny * nx, n_members, resident_ctas(morph_forward_kernel)), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       u, u_ref, ext, n_blocks, n_members, ny, nx, n_iter, tol);
   return finish(who);
 }
@@ -222,7 +234,7 @@ extern "C" fftenkf_status fftenkf_morph_reference(const float* ext, float* ext_r
   if (overlaps(ext, (size_t)n_channels * n_members * plane * sizeof(float), ext_ref,
                (size_t)n_channels * plane * sizeof(float)))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": ext_ref overlaps ext");
-  morph_reference_kernel<<<grid_for((size_t)n_channels * plane), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_reference_kernel<<<grid_for((size_t)n_channels * plane, resident_ctas(morph_reference_kernel)), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       ext, ext_ref, n_channels, n_members, plane);
   return finish(who);
 }
@@ -239,7 +251,7 @@ extern "C" fftenkf_status fftenkf_morph_inverse(const float* ext, const float* u
   if (overlaps(u_out, out_bytes, ext, (size_t)(n_blocks + 2) * n_members * plane) ||
       overlaps(u_out, out_bytes, u_ref, (size_t)n_blocks * plane))
     return mfail(FFTENKF_EINVAL, std::string(who) + ": u_out overlaps an input");
-  morph_inverse_kernel<<<member_grid(ny * nx, n_members, kResidentInverse), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  morph_inverse_kernel<<<member_grid(ny * nx, n_members, resident_ctas(morph_inverse_kernel)), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       ext, u_ref, u_out, n_blocks, n_members, ny, nx);
   return finish(who);
 }

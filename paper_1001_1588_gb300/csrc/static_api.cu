@@ -79,13 +79,37 @@ fftenkf_status scratch_address(char** out) {
 
 }  // namespace
 
+// the status word sits at offset 0 of the array (see the layout below)
+extern "C" fftenkf_status fftenkf_static_last_device_status(void* stream) {
+  set_last_error("");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return sfail(FFTENKF_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return sfail(FFTENKF_EUNSUPPORTED, "device index out of range");
+  e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return sfail(FFTENKF_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    base = static_cast<char*>(g_scratch_ptr[dev]);
+  }
+  if (!base) return FFTENKF_OK;   // no call on this device yet
+  int word = 0;
+  e = cudaMemcpy(&word, base, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(base, 0, sizeof(int));
+  if (e != cudaSuccess) return sfail(FFTENKF_ECUDA, std::string("status word: ") + cudaGetErrorString(e));
+  if (word & kStatusTimeout) return sfail(FFTENKF_ETIMEOUT, "a bounded wait for an asynchronous copy gave up");
+  if (word & kStatusNonFinite) return sfail(FFTENKF_ENONFINITE, "non-finite spectral covariance");
+  return FFTENKF_OK;
+}
+
 extern "C" fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble, int ny, int nx, int n_members,
                                                            int storage, double* spectrum_out, void* stream) {
   set_last_error("");
   if (!ensemble || !spectrum_out) return sfail(FFTENKF_EINVAL, "null argument");
   if (((uintptr_t)ensemble | (uintptr_t)spectrum_out) % 16) return sfail(FFTENKF_EINVAL, "pointers must be 16-byte aligned");
   if (storage != FFTENKF_F32 && storage != FFTENKF_BF16) return sfail(FFTENKF_EINVAL, "unknown storage");
-  if (n_members < 2) return sfail(FFTENKF_EUNSUPPORTED, "need at least 2 members (eq. dii divides by N-1)");
+  if (n_members < 2) return sfail(FFTENKF_EUNSUPPORTED, "need at least 2 members (the covariance divides by N-1)");
   if (nx % 2 || nx < 16 || nx > 8192 || !row_line_supported(nx / 2) || ny < 16 || ny > 4096 || !line_supported(ny))
     return sfail(FFTENKF_EUNSUPPORTED, "ny, nx must be 2^a or 3*2^a (16 <= nx <= 8192, 16 <= ny <= 4096)");
   if (col_stats_smem(ny, 1, 0, nullptr) == 0) return sfail(FFTENKF_EUNSUPPORTED, "column statistics do not fit in shared memory");

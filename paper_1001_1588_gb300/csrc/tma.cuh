@@ -82,10 +82,13 @@ __device__ __forceinline__ void tensor_load_3d(void* dst, const CUtensorMap* map
 }
 
 // CTA-wide wait for `parity` of `bar`, observed by thread 0.  Returns false
-// (for every thread) after a timeout; the caller must then return.
-__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status, int* flag) {
+// (for every thread) after a timeout; the caller must then return.  expire
+// (a test setting) makes the wait give up at once, as an expired one does:
+// the timeout is recorded and the copies in flight are drained before the
+// CTA leaves.
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status, int* flag, bool expire = false) {
   if (threadIdx.x == 0) {
-    bool ok = mbar_wait_bounded(bar, parity);
+    bool ok = !expire && mbar_wait_bounded(bar, parity);
     if (!ok) {
       atomicOr(status, kStatusTimeout);
       mbar_wait_bounded(bar, parity);  // let copies in flight land before leaving
