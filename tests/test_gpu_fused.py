@@ -68,6 +68,8 @@ def _run(p, sel):
         (4096, 32, 4, [1, 1, 0, 0], "f32"),
         (4096, 64, 5, [1, 1, 0, 0], "bf16"),
         (1024, 1024, 3, [1], "f32"),             # single block
+        (256, 4096, 3, [1, 1, 0, 0], "bf16"),    # 4096-wide rows: anomaly + innovation rows in one pass
+        (512, 1024, 4, [1, 0, 1, 0], "f32"),     # the same pass with FP32 members
     ],
 )
 def test_fused_parity(ny, nx, N, observed, storage, sel):

@@ -69,6 +69,40 @@ def test_forward_matches_oracle(M, K, ny, nx, n_iter, tol):
     assert np.abs(ext[2:] - ref).max() <= ATOL
 
 
+def _lipschitz_inf(f):
+    """Max-norm Lipschitz constant of the bilinear interpolant of the periodic field(s) f [..][ny][nx]
+    along each axis: the largest node difference (the interpolant's partial derivatives)."""
+    f = np.asarray(f, np.float64)
+    dx = np.abs(np.roll(f, -1, axis=-1) - f).max()
+    dy = np.abs(np.roll(f, -1, axis=-2) - f).max()
+    return dx, dy
+
+
+def test_forward_stopping_rule_near_converged_fixed_point():
+    """The kernel stops a point after the first step that moves it by at most tol = 1e-5 cells; the
+    oracle's converged inverse mapping (tol = 0, 80 steps: every iterate repeats) is the fixed point
+    q* = p - T(q*).  For the iteration map q -> p - T(q) with max-norm Lipschitz constant kappa < 1
+    (kappa <= max over components of |dT/dx| + |dT/dy|), a step of size delta <= tol leaves the
+    iterate within kappa delta / (1 - kappa) of q*, and the residual r = u(q) - u_ref moves by at most
+    |du/dx| + |du/dy| times that.  The GPU residuals must lie within that bound plus the FP32 rounding
+    allowance of the other tests (ATOL)."""
+    M, K, ny, nx, tol = 2, 4, 128, 160, 1e-5
+    u, u_ref, T = _inputs(M, K, ny, nx, 2.5, 211)
+    ext = _gpu_forward(u, u_ref, T, 20, tol)
+    ref = morph.morph_forward(u, u_ref, T, 80, 0.0)
+    kappa = 0.0
+    for k in range(K):
+        for c in range(2):
+            dx, dy = _lipschitz_inf(T[c, k])
+            kappa = max(kappa, dx + dy)
+    assert kappa < 1.0, kappa
+    gu = max(sum(_lipschitz_inf(u[j, k])) for j in range(M) for k in range(K))
+    bound = gu * tol * kappa / (1.0 - kappa)
+    err = np.abs(ext[2:] - ref).max()
+    assert err <= ATOL + bound, (err, bound, kappa)
+    assert _rel(ext[2:], ref) <= TOL
+
+
 def test_forward_integer_shift_exact():
     M, K, ny, nx = 2, 3, 24, 40
     u, u_ref, _ = _inputs(M, K, ny, nx, 1.0, 7)
