@@ -54,10 +54,13 @@ def parse():
     ap.add_argument("--no-seeded", action="store_true", help="skip the timing of the seeded (drawn-perturbation) analysis")
     ap.add_argument("--no-side", action="store_true",
                     help="sine workload: skip the side timing of the periodic extension-size analysis")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "coupled", "sine", "morph"],
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP32-storage run of the headline draw (the equal-RMSE precision comparison)")
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "coupled", "sine", "morph", "compare"],
                     help="large: 4 blocks 4096^2 N=20 (default, the headline); batched: 256 mixed analyses; "
                          "coupled: 3 blocks 4096^2 N=20 with coupled observed blocks; "
                          "sine: real sine transform variant on 2049^2 nodes, 4 blocks, N=20; "
+                         "compare: precision, learned-spectrum and batched forms at equal analysis RMSE; "
                          "morph: morphing FFT EnKF, 2 blocks 4096^2 N=20 FP32 (T_x, T_y, r^(1) observed)")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
@@ -336,6 +339,209 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------ our arm
+def analysis_rmse(ens, truth):
+    """RMSE of the ensemble mean against the truth, per block and over all blocks:
+    sqrt(mean_x (mean_k u_k(x) - truth(x))^2) (the evaluation of the learned-spectrum config)."""
+    mean = ens.float().mean(dim=1)
+    err = (mean - truth.float()) ** 2
+    return [float(x) for x in err.mean(dim=(1, 2)).sqrt()], float(err.mean().sqrt())
+
+
+def compare_precision(dev, ny, nx, Nm, steps=5, warmup=3):
+    """The headline draw analysed with FP32 and with BF16 member storage (the BF16 members are the
+    FP32 ones rounded): ms per analysis and the analysis RMSE against the truth of each, on the same
+    draw, so that throughput is compared at (near) equal RMSE."""
+    import torch
+    from paper_1001_1588_gb300 import torch_api
+    from synth.fields_torch import make_config3_torch
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        prob = make_config3_torch(device=dev, ny=ny, nx=nx, N=Nm, storage=dt)
+        plan = torch_api.Plan(ny, nx, M, Nm, dt, OBSERVED)
+        plan.workspace(dev)
+        f_blocks, f_total = analysis_rmse(prob.ensemble, prob.truth)
+        ens = prob.ensemble.clone()
+        plan.analyze(ens, prob.data, prob.perturbations, prob.rhat)    # the analysis of the draw itself
+        a_blocks, a_total = analysis_rmse(ens, prob.truth)
+        for _ in range(warmup):
+            plan.analyze(ens, prob.data, prob.perturbations, prob.rhat)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            plan.analyze(ens, prob.data, prob.perturbations, prob.rhat)
+        t1.record(stream)
+        t1.synchronize()
+        st = plan.device_status()
+        plan.close()
+        out[name] = {"ms_per_analysis": t0.elapsed_time(t1) / steps, "rmse_forecast": f_total,
+                     "rmse_analysis": a_total, "rmse_analysis_blocks": a_blocks, "rmse_forecast_blocks": f_blocks,
+                     "status": st}
+        del prob, ens
+        torch.cuda.empty_cache()
+    out["speedup_bf16_over_f32"] = out["f32"]["ms_per_analysis"] / out["bf16"]["ms_per_analysis"]
+    out["rmse_rel_diff_bf16_vs_f32"] = (out["bf16"]["rmse_analysis"] - out["f32"]["rmse_analysis"]) / out["f32"]["rmse_analysis"]
+    return out
+
+
+def compare_batched(dev, count=256, steps=5):
+    """The batched draw in FP32 and in BF16 storage: ms per batch (autotuned, graph-replayed) and the
+    mean over items of the analysis RMSE against each item's truth, on the same draw."""
+    import numpy as np
+    import torch
+    from paper_1001_1588_gb300 import abi
+    from synth.fields_torch import make_batched_torch
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for name, dt, code in (("f32", torch.float32, abi.FFTENKF_F32), ("bf16", torch.bfloat16, abi.FFTENKF_BF16)):
+        items = make_batched_torch(device=dev, count=count, storage=dt)
+        ens0 = [it.ensemble.clone() for it in items]
+        b = abi.fftenkf_plan_batched([(it.ny, it.nx, it.N) for it in items], code)
+        ws = torch.empty(abi.fftenkf_batch_workspace_size(b), dtype=torch.uint8, device=dev)
+        abi.fftenkf_batch_autotune(b, ws, 0)
+        for it, e0 in zip(items, ens0):
+            it.ensemble.copy_(e0)
+
+        def step():
+            abi.fftenkf_analyze_batched(b, [it.ensemble for it in items], [it.data for it in items],
+                                        [it.perturbations for it in items], [it.rhat for it in items], ws,
+                                        int(stream.cuda_stream))
+
+        step()
+        rm_f = float(np.mean([analysis_rmse(e0[None], it.truth[None])[1] for it, e0 in zip(items, ens0)]))
+        rm_a = float(np.mean([analysis_rmse(it.ensemble[None], it.truth[None])[1] for it in items]))
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            step()
+        t1.record(stream)
+        t1.synchronize()
+        st = abi.fftenkf_batch_last_device_status(b, int(stream.cuda_stream))
+        abi.fftenkf_batch_destroy(b)
+        out[name] = {"ms_per_batch": t0.elapsed_time(t1) / steps, "rmse_forecast_mean": rm_f,
+                     "rmse_analysis_mean": rm_a, "status": st}
+    out["speedup_bf16_over_f32"] = out["f32"]["ms_per_batch"] / out["bf16"]["ms_per_batch"]
+    out["rmse_rel_diff_bf16_vs_f32"] = (out["bf16"]["rmse_analysis_mean"] - out["f32"]["rmse_analysis_mean"]) / out["f32"]["rmse_analysis_mean"]
+    return out
+
+
+def compare_learned(dev, grid=1024, pairs=4096, epochs=12, n_draws=32, steps=5):
+    """Learned against plain spectrum at grid^2, N = 5 (the learned-spectrum config): the MLP is
+    trained on the GPU by the library's kernels on `pairs` (N = 5 estimate, N = 500 target) pairs,
+    then analysis RMSE over held-out draws for the plain estimate, the learned spectrum and the true
+    generating spectrum; ms per analysis of the plain path and of the learned path (estimate,
+    denoise, analysis with the supplied spectrum)."""
+    import math
+    import torch
+    from paper_1001_1588_gb300 import abi, denoiser, torch_api
+    t0 = time.time()
+    pr = denoiser.Pairs(grid, grid)
+    X, Y = pr.generate(pairs, seed=20260005)
+    pr.close()
+    params, _, _, step_, hist = denoiser.train(X, Y, epochs, 256, 1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    ev, _ = denoiser.evaluate(params, grid, grid, n_draws=n_draws)
+    # timing of one analysis each way on a draw of the same family
+    stream = torch.cuda.current_stream(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(99)
+    S = denoiser.powerlaw_half(grid, grid, 8.0, -3.5, dev)
+    ens = denoiser.draw_fields(S, 5, gen, grid, grid)[None].contiguous()
+    truth = denoiser.draw_fields(S, 1, gen, grid, grid)[0]
+    data = (truth + math.sqrt(0.1) * torch.randn(grid, grid, device=dev, generator=gen))[None].contiguous()
+    pert = (math.sqrt(0.1) * torch.randn(5, 1, grid, grid, device=dev, generator=gen)).contiguous()
+    rhat = torch.full((1, grid, grid // 2 + 1), 0.1, dtype=torch.float64, device=dev)
+    plan = torch_api.Plan(grid, grid, 1, 5, torch.float32, [1])
+    den = abi.fftenkf_denoiser_create(grid, grid, 5)
+    learned = torch.empty(grid * (grid // 2 + 1), dtype=torch.float64, device=dev)
+
+    def plain():
+        plan.analyze(ens, data, pert, rhat)
+
+    def with_learned():
+        chat = plan.estimate_spectrum(ens)
+        abi.fftenkf_denoise_spectrum(den, params, chat, learned, 5, int(stream.cuda_stream), want_flag=False)
+        plan.analyze(ens, data, pert, rhat, learned)
+
+    times = {}
+    for name, fn in (("plain", plain), ("learned", with_learned)):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        times[name] = e0.elapsed_time(e1) / steps
+    plan.close()
+    abi.fftenkf_denoiser_destroy(den)
+    # the plain estimate with more members: the ensemble size at which it matches the learned
+    # spectrum's RMSE at N = 5, and what that ensemble costs per analysis
+    sweep = plain_members_sweep(dev, grid, (5, 10, 20, 40), n_draws=n_draws)
+    match = next((n for n, v in sweep.items() if v["rmse"] <= ev["learned"]), None)
+    return {"grid": grid, "members": 5, "pairs": pairs, "epochs": epochs, "train_steps": step_,
+            "train_loss": hist[-1], "seconds_pairs_and_train": t_train, "eval": ev,
+            "ms_per_analysis_plain": times["plain"], "ms_per_analysis_learned": times["learned"],
+            "plain_by_members": sweep, "plain_members_matching_learned_rmse": match}
+
+
+def plain_members_sweep(dev, grid, Ns, n_draws=32, r=0.1, seed=777, steps=5):
+    """Analysis RMSE (mean over held-out draws of the learned-spectrum family: power-law spectra,
+    ell log-uniform in [2, 64], slope uniform in [-5, -2], rhat = r) and ms per analysis of the plain
+    FFT EnKF with N members, for each N in Ns."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1001_1588_gb300 import denoiser, torch_api
+    stream = torch.cuda.current_stream(dev)
+    rhat = torch.full((1, grid, grid // 2 + 1), r, dtype=torch.float64, device=dev)
+    out = {}
+    for N in Ns:
+        rng = np.random.default_rng(seed)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed + N)
+        plan = torch_api.Plan(grid, grid, 1, N, torch.float32, [1])
+        rm = []
+        for _ in range(n_draws):
+            ell = float(np.exp(rng.uniform(np.log(2.0), np.log(64.0))))
+            beta = float(rng.uniform(-5.0, -2.0))
+            S = denoiser.powerlaw_half(grid, grid, ell, beta, dev)
+            truth = denoiser.draw_fields(S, 1, gen, grid, grid)[0]
+            ens = denoiser.draw_fields(S, N, gen, grid, grid)[None].contiguous()
+            data = (truth + math.sqrt(r) * torch.randn(grid, grid, device=dev, generator=gen))[None].contiguous()
+            pert = (math.sqrt(r) * torch.randn(N, 1, grid, grid, device=dev, generator=gen)).contiguous()
+            plan.analyze(ens, data, pert, rhat)
+            rm.append(float(torch.sqrt(((ens[0].mean(dim=0) - truth) ** 2).mean()).item()))
+        for _ in range(3):
+            plan.analyze(ens, data, pert, rhat)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.analyze(ens, data, pert, rhat)
+        e1.record(stream)
+        e1.synchronize()
+        plan.close()
+        out[N] = {"rmse": float(np.mean(rm)), "ms_per_analysis": e0.elapsed_time(e1) / steps}
+    return out
+
+
+def run_compare(a):
+    """One JSON line with the comparisons of the precision, learned-spectrum and batched forms with
+    the plain FP32 FFT EnKF at (near) equal analysis RMSE."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    res = {"metric": "equal-RMSE comparisons (analysis RMSE of the ensemble mean vs truth, ms per analysis)",
+           "workload": "compare", "n_gpus": 1, "data": "synthetic"}
+    res["precision_4x4096x4096_N20"] = compare_precision(dev, a.ny, a.nx, a.members)
+    res["batched_256"] = compare_batched(dev, a.batch)
+    res["learned_1024_N5"] = compare_learned(dev)
+    print(json.dumps(res))
+    return 0
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -472,6 +678,12 @@ def run_ours(a):
         del d_in, h_in, h_out
 
     # the same analyses with the perturbations drawn by the library (fftenkf_analyze_seeded)
+    equal_rmse = None
+    if not a.no_compare and world == 1:
+        try:
+            equal_rmse = compare_precision(dev, ny, nx, Nm)
+        except Exception as exc:   # reported, not fatal to the headline line
+            equal_rmse = {"error": str(exc)[:200]}
     seeded = None
     if not a.no_seeded:
         for _ in range(max(a.warmup, 1)):
@@ -521,6 +733,7 @@ def run_ours(a):
             "cpu_baseline": cpu,
             "cufft_reference": cufft,
             "seeded": seeded,
+            "equal_rmse_precision": equal_rmse,
             "source_sha": source_sha(),
         }
         print(json.dumps(out))
@@ -864,6 +1077,8 @@ def main():
         return run_sine(a)
     if a.workload == "morph":
         return run_morph(a)
+    if a.workload == "compare":
+        return run_compare(a)
     return run_ours(a)
 
 

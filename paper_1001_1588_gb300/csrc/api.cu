@@ -74,7 +74,7 @@ struct fftenkf_plan_s {
   bool tm_ok = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // workspace layout (byte offsets)
-  size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, off_rhat_t, ws_bytes;
+  size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, off_rhat_t, off_amp, ws_bytes;
   void* own_ws = nullptr;
   int device = 0;
   // per-pass CUDA-event timing (fftenkf_set_profiling); a ring of event pairs per pass
@@ -155,6 +155,7 @@ static void layout(fftenkf_plan_s* p) {
   p->off_goo = off;  off = round_up(off + (size_t)p->n_obs * tab * sizeof(float), 256);
   p->off_gjo = off;  off = round_up(off + gain_tables * tab * sizeof(float2), 256);
   p->off_rhat_t = off; off = round_up(off + (size_t)p->n_obs * tab * sizeof(double), 256);
+  p->off_amp = off;  off = round_up(off + (size_t)p->n_obs * tab * sizeof(float), 256);
   p->ws_bytes = off;
 }
 
@@ -459,9 +460,14 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
     if (e == cudaSuccess) e = launch_rhat_transpose(rhat, rhat_t, p->n_obs, p->ny, p->L, p->aux);
     prof_end(p, kPassRhatT, p->aux);
   }
+  const bool fused = !spectrum && p->use_fused();
+  float* amp_t = reinterpret_cast<float*>(ws + p->off_amp);
   if (!spectrum) {
+    // the fused pass draws perturbations with the FP32 amplitudes sqrt(ny nx rhat) of the same pass
     prof_begin(p, kPassRhatT, p->aux);
-    if (e == cudaSuccess) e = launch_rhat_transpose(rhat, rhat_t, p->n_obs, p->ny, p->L, p->aux);
+    if (e == cudaSuccess)
+      e = launch_rhat_transpose(rhat, rhat_t, p->n_obs, p->ny, p->L, p->aux, (fused && drawn) ? amp_t : nullptr,
+                                (float)std::sqrt((double)p->ny * (double)p->nx));
     prof_end(p, kPassRhatT, p->aux);
   } else {
     prof_begin(p, kPassGain, p->aux);
@@ -469,7 +475,6 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
     prof_end(p, kPassGain, p->aux);
   }
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
-  const bool fused = !spectrum && !drawn && p->use_fused();
   if (fused) {
     // mean and anomaly rows now; the columns after the innovation rows
     if (e == cudaSuccess) e = run_mean_rows(p, ensemble, ws, s);
@@ -527,6 +532,9 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
     ColFusedParams f = fused_params(p, ws);
     f.W = rp.out;
     f.rhat_t = rhat_t;
+    f.drawn = drawn ? 1 : 0;
+    f.seed = seed;
+    f.amp_t = amp_t;
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
     prof_begin(p, kPassFused, s);
     if (e == cudaSuccess) e = launch_col_fused(f, s);

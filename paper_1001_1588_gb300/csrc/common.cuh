@@ -188,6 +188,11 @@ struct ColFusedParams {
   float inv_G;            // 1 / (ny nx)
   int* status;
   int vsel;               // line-FFT schedule: 0 = wide (V = 16), 1 = narrow (V = 8, twice the threads)
+  // perturbations drawn here (seeded analysis; the innovation rows are then d - u): what_{k,i} +=
+  // amp_i zhat_{k,i}, zhat from Philox4x32-10 under `seed` (stream k n_obs + i), amp = sqrt(ny nx rhat)
+  int drawn;
+  unsigned long long seed;
+  const float* amp_t;     // [n_obs][L+1][ny]
 };
 // launch of the fused column pass; cudaErrorNotSupported when the shape is not covered
 cudaError_t launch_col_fused(const ColFusedParams& p, cudaStream_t s);
@@ -227,8 +232,9 @@ struct ChatOutMap {
 ChatOutMap chat_out_map(int n_obs, int n_un, int coupled, const int* obs, const int* un, int M);
 cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, const ChatOutMap& map,
                             cudaStream_t s);
-// rhat [n][ny][L+1] -> rhat_t [n][L+1][ny]
-cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s);
+// rhat [n][ny][L+1] -> rhat_t [n][L+1][ny]; with amp also amp [n][L+1][ny] = sqrt_G sqrt(rhat) (FP32)
+cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s,
+                                  float* amp = nullptr, float sqrt_G = 0.f);
 bool line_supported(int n);       // column line lengths
 bool row_line_supported(int n);   // row line lengths (nx/2)
 // shared-memory bytes a pass needs (0 = unsupported), for plan-time checks

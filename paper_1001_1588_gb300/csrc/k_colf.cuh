@@ -25,6 +25,7 @@
 #pragma once
 #include "common.cuh"
 #include "fft_pair.cuh"
+#include "perturb.cuh"
 #include "tma.cuh"
 #include "tmem.cuh"
 
@@ -258,7 +259,50 @@ __device__ __forceinline__ void fused_targets(cp (&s)[V], int tp, int M, int n_o
   }
 }
 
+// Perturbations drawn in frequency space added to the innovation spectra of member k (seeded
+// analysis): half i of w gets amp_i(k_y, c) zhat_{k,i}(k_y, c), zhat from Philox4x32-10 counters and
+// Box-Muller (perturb.cuh), on the same counter layout as the separate column update.
 template <int NY, int V, int NOBS>
+__device__ __forceinline__ void fused_add_drawn(cp (&w)[V], const ColFusedParams& p, int k, int c, int t) {
+  constexpr int T = NY / V;
+  const size_t tab = (size_t)(p.L + 1) * NY;
+#pragma unroll
+  for (int i = 0; i < NOBS; ++i) {
+    if (i >= p.n_obs) continue;
+    const int stream = k * p.n_obs + i;
+    const float* amp = p.amp_t + (size_t)i * tab + (size_t)c * NY + t;
+    if (c != 0 && c != p.L) {
+      // one generator call serves k_y (words 0, 1) and k_y + ny/2 (words 2, 3): slots m and m + V/2
+      const float h = 0.70710678118654752f;
+#pragma unroll
+      for (int m = 0; m < V / 2; ++m) {
+        const uint4 w4 = philox4x32_10(make_uint4((uint32_t)(t + T * m), (uint32_t)c, (uint32_t)stream, 0u),
+                                       (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+        const float2 zl = box_muller(w4.x, w4.y), zh = box_muller(w4.z, w4.w);
+        const float al = h * __ldg(amp + T * m), ah = h * __ldg(amp + T * (m + V / 2));
+        float2 a = i ? half_of<1>(w[m]) : half_of<0>(w[m]);
+        float2 b = i ? half_of<1>(w[m + V / 2]) : half_of<0>(w[m + V / 2]);
+        a = make_float2(fmaf(al, zl.x, a.x), fmaf(al, zl.y, a.y));
+        b = make_float2(fmaf(ah, zh.x, b.x), fmaf(ah, zh.y, b.y));
+        if (i) { set_half<1>(w[m], a); set_half<1>(w[m + V / 2], b); }
+        else { set_half<0>(w[m], a); set_half<0>(w[m + V / 2], b); }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < V; ++m) {
+        const float am = __ldg(amp + T * m);
+        const float2 z = white_edge(p.seed, stream, t + T * m, c, NY);
+        float2 a = i ? half_of<1>(w[m]) : half_of<0>(w[m]);
+        a = make_float2(fmaf(am, z.x, a.x), fmaf(am, z.y, a.y));
+        if (i) set_half<1>(w[m], a); else set_half<0>(w[m], a);
+      }
+    }
+  }
+}
+
+// DRAWN: perturbations drawn here (seeded analysis); a separate instantiation, so that the analysis
+// with given perturbations carries none of the generator's code
+template <int NY, int V, int NOBS, bool DRAWN>
 __global__ void __launch_bounds__(V <= 8 ? 512 : 256, 1) col_fused_kernel(const __grid_constant__ ColFusedParams p) {
   using Sh = ColFusedShape<NY, V>;
   constexpr int T = Sh::T;
@@ -375,6 +419,7 @@ __global__ void __launch_bounds__(V <= 8 ? 512 : 256, 1) col_fused_kernel(const 
       } else {
         const int k = u - units_stats;
         fft_pair<NY, V, false, true>(v, xbuf, t, p.tw, bid);   // what; the buffer is reused at once
+        if constexpr (DRAWN) fused_add_drawn<NY, V, NOBS>(v, p, k, c, t);
         store_halves<V>(v, ta + KB);
 #pragma unroll 1
         for (int tp = 0; tp < P; ++tp) {
@@ -442,7 +487,7 @@ inline cudaError_t col_fused_NYS(const ColFusedParams& p, cudaStream_t st) {
   constexpr int V = plan_V(NY, SEL);
   const ColFusedLaunch s = col_fused_launch(NY, SEL);
   if (s.lpc < 1 || s.V != V) return cudaErrorNotSupported;
-  auto kern = col_fused_kernel<NY, V, NOBS>;
+  auto kern = p.drawn ? col_fused_kernel<NY, V, NOBS, true> : col_fused_kernel<NY, V, NOBS, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
   if (e != cudaSuccess) return e;
   const int groups = (p.L + 1 + s.lpc - 1) / s.lpc;

@@ -192,8 +192,10 @@ cudaError_t launch_chat_out(const float* chat_t, double* out, int ny, int L, con
   return cudaGetLastError();
 }
 
+// rhat [n][ny][L1] -> rhat_t [n][L1][ny]; with amp non-null also amp [n][L1][ny] = sqrt_G sqrt(rhat) in
+// FP32, the amplitude of the perturbations drawn in frequency space
 __global__ void __launch_bounds__(256) rhat_transpose_kernel(const double* __restrict__ in, double* __restrict__ out,
-                                                             int ny, int L1) {
+                                                             int ny, int L1, float* __restrict__ amp, float sqrt_G) {
   __shared__ double tile[TB][TB + 1];
   const int c0 = blockIdx.x * TB, ky0 = blockIdx.y * TB;
   const size_t K = (size_t)ny * L1;
@@ -206,13 +208,18 @@ __global__ void __launch_bounds__(256) rhat_transpose_kernel(const double* __res
   __syncthreads();
   for (int cc = threadIdx.y; cc < TB; cc += blockDim.y) {
     const int c = c0 + cc, ky = ky0 + threadIdx.x;
-    if (c < L1 && ky < ny) dst[(size_t)c * ny + ky] = tile[threadIdx.x][cc];
+    if (c < L1 && ky < ny) {
+      const double r = tile[threadIdx.x][cc];
+      dst[(size_t)c * ny + ky] = r;
+      if (amp) amp[blockIdx.z * K + (size_t)c * ny + ky] = sqrt_G * sqrtf((float)r);
+    }
   }
 }
 
-cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s) {
+cudaError_t launch_rhat_transpose(const double* rhat, double* rhat_t, int n, int ny, int L, cudaStream_t s,
+                                  float* amp, float sqrt_G) {
   dim3 grid((L + 1 + TB - 1) / TB, (ny + TB - 1) / TB, n);
-  rhat_transpose_kernel<<<grid, dim3(TB, 8), 0, s>>>(rhat, rhat_t, ny, L + 1);
+  rhat_transpose_kernel<<<grid, dim3(TB, 8), 0, s>>>(rhat, rhat_t, ny, L + 1, amp, sqrt_G);
   return cudaGetLastError();
 }
 

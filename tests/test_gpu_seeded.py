@@ -48,16 +48,25 @@ def _oracle_pert(p, seed):
     return perturb.perturbations(p.ny, p.nx, p.rhat, seed, p.N)
 
 
-@pytest.mark.parametrize("which", ["config1", "config2", "config3_bf16", "config3_f32"])
+@pytest.mark.parametrize("which", ["config1", "config2", "config3_bf16", "config3_f32",
+                                   "config3_fused_bf16", "config3_fused_f32", "config2_fused"])
 def test_seeded_analysis_matches_oracle(which):
+    # the *_fused shapes (columns of 512 or more points, 1-2 observed blocks) draw the
+    # perturbations inside the fused column pass, the others inside the separate column update
     if which == "config1":
         p, tol = fields.make_config1(ny=64, nx=64), TOL32
     elif which == "config2":
         p, tol = fields.make_config2(ny=128, nx=256), TOL32
     elif which == "config3_bf16":
         p, tol = fields.make_config3(ny=64, nx=96, N=6, storage="bf16"), TOL16
-    else:
+    elif which == "config3_f32":
         p, tol = fields.make_config3(ny=96, nx=64, N=5, storage="f32"), TOL32
+    elif which == "config3_fused_bf16":
+        p, tol = fields.make_config3(ny=1024, nx=64, N=6, storage="bf16"), TOL16
+    elif which == "config3_fused_f32":
+        p, tol = fields.make_config3(ny=4096, nx=32, N=4, storage="f32"), TOL32
+    else:
+        p, tol = fields.make_config2(ny=512, nx=128), TOL32
     ua, st = _seeded(p, SEED)
     assert st == 0
     e = _oracle_pert(p, SEED)
