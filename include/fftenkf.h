@@ -256,7 +256,10 @@ fftenkf_status fftenkf_batch_last_device_status(fftenkf_batch batch, void* strea
  * back to every wavenumber.  Parameters: one flat float vector of
  * fftenkf_mlp_param_count() values [W1 (64x256, row = output), b1, W2 (64x64),
  * b2, W3, b3, W4 (128x64), b4]; forward and backward use their BF16 rounding.
- * All array arguments are device pointers; spectra are [ny][nx/2+1] double. */
+ * All array arguments are device pointers; spectra are [ny][nx/2+1] double.
+ * A denoiser holds device scratch that fftenkf_denoiser_features and fftenkf_denoise_spectrum
+ * write: calls on one denoiser must be ordered (one stream, or synchronised between streams);
+ * separate denoisers run concurrently. */
 typedef struct fftenkf_denoiser_s* fftenkf_denoiser;
 int fftenkf_mlp_param_count(void);
 fftenkf_status fftenkf_denoiser_create(fftenkf_denoiser* d, int ny, int nx, int trained_members);

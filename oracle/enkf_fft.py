@@ -1,9 +1,9 @@
-"""FFT EnKF analysis of a few members at full size, in FP64 with numpy's FFT as the transform step
+"""FFT EnKF analysis of a few members at full size, in FP64 with a library FFT as the transform step
 (oracle; test infrastructure, imported only by the tests).
 
 The explicit-DFT oracle (enkf.py) costs O(G (nx + ny)) per field, too slow for a 4096 x 4096 state of
-80 fields.  This module computes the same quantities with a library real FFT (numpy.fft.rfft2 /
-irfft2, unitary scaling, FP64) as the step F, on the half spectrum [ny][nx/2+1], and streams the
+80 fields.  This module computes the same quantities with a library real FFT (scipy.fft / numpy.fft
+rfft2 and irfft2, unitary scaling, FP64) as the step F, on the half spectrum [ny][nx/2+1], and streams the
 members one field at a time so that only the covariance sums and a few spectra are held:
 
   1. chat^(oo) = 1/(N-1) sum_k |F(u_k^(o) - ubar^(o))|^2 and chat^(jo) = 1/(N-1) sum_k
@@ -21,17 +21,28 @@ enkf.analyze on small grids in tests/test_oracle_fft_path.py.
 
 from __future__ import annotations
 
+import os
 from typing import Callable, Dict, Sequence
 
 import numpy as np
 
 
-def _rfft2(x: np.ndarray) -> np.ndarray:
-    return np.fft.rfft2(np.asarray(x, dtype=np.float64), norm="ortho")
+try:   # the same transform, threaded over the host's cores where scipy is present
+    import scipy.fft as _sfft
 
+    _WORKERS = os.cpu_count() or 1
 
-def _irfft2(X: np.ndarray, shape) -> np.ndarray:
-    return np.fft.irfft2(X, s=shape, norm="ortho")
+    def _rfft2(x: np.ndarray) -> np.ndarray:
+        return _sfft.rfft2(np.asarray(x, dtype=np.float64), norm="ortho", workers=_WORKERS)
+
+    def _irfft2(X: np.ndarray, shape) -> np.ndarray:
+        return _sfft.irfft2(X, s=shape, norm="ortho", workers=_WORKERS)
+except ImportError:  # pragma: no cover
+    def _rfft2(x: np.ndarray) -> np.ndarray:
+        return np.fft.rfft2(np.asarray(x, dtype=np.float64), norm="ortho")
+
+    def _irfft2(X: np.ndarray, shape) -> np.ndarray:
+        return np.fft.irfft2(X, s=shape, norm="ortho")
 
 
 def covariance_sums(field: Callable[[int, int], np.ndarray], M: int, N: int, observed: Sequence[int]):

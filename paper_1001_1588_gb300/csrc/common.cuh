@@ -241,4 +241,17 @@ bool row_line_supported(int n);   // row line lengths (nx/2)
 size_t col_stats_smem(int ny, int nf, int vsel, int* lpc);
 size_t col_update_smem(int ny, int n_obs, int vsel, int* lpc, int* n_stages);
 
+// Radial bins of the learned denoiser (device tables, built once per grid) and the scratch of
+// its segmented binning.
+struct MlpBins {
+  int K1, nseg, max_batch;
+  const uint32_t* order;     // [K1] entries grouped by bin
+  const uint32_t* start;     // [129] bin offsets into order
+  const uint32_t* seg_off;   // [nseg + 1] segment offsets into order (each within one bin)
+  const uint32_t* bin_seg;   // [129] first segment of every bin
+  const float* centre_log;   // [128]
+  unsigned* cmax_bits;       // [max_batch] scratch
+  float* part;               // [max_batch][nseg] scratch
+};
+
 }  // namespace fftenkf

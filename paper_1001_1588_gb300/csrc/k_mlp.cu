@@ -7,6 +7,8 @@
 // BF16 network and are applied to the FP32 master copy).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fftenkf {
@@ -20,55 +22,102 @@ constexpr int kActs = kIn + 3 * kH + kOut;   // per sample: x | z1 | z2 | z3 | o
 constexpr int SB = 8;                        // samples per CTA
 
 // ----------------------------------------------------------------- binning
-// chat: [B][ny][L+1] f64 (one real table per sample); bins: [ny][L+1] uint8 bin
-// index (FP64 decision, made on the host); feat: [B][256] f32; mean: [B] f32
-// bin_order: the K1 half-spectrum entries grouped by bin (ascending), bin_start[129]
-// their offsets: every warp reduces whole bins (lane partial sums, then a tree
-// over the lanes), so no floating-point atomics and a short summation chain.
-__global__ void __launch_bounds__(256) mlp_bin_kernel(const double* __restrict__ chat,
-                                                      const uint32_t* __restrict__ bin_order,
-                                                      const uint32_t* __restrict__ bin_start,
-                                                      const float* __restrict__ centre_log, int K1,
-                                                      float* __restrict__ feat, float* __restrict__ mean) {
-  // log(max(c, 1e-30 cmax)) is evaluated as log(max(c/cmax, 1e-30)) + log(cmax)
-  // so that the floor never underflows; one conversion to float per entry
-  __shared__ float vals[kBins];
-  __shared__ float red[256];
-  __shared__ float mu_s;
-  const double* c = chat + (size_t)blockIdx.x * K1;
+// chat: [B][ny][L+1] f64 (one real table per sample); feat: [B][256] f32; mean: [B] f32.
+// The bins are fixed per grid (FP64 decision, made on the host): bin_order lists the K1
+// half-spectrum entries grouped by bin (ascending), bin_start[129] their offsets.  Each bin is
+// cut into segments of at most kSegLen entries (seg_off[nseg+1], bin_seg[129] the segments of
+// every bin), so that one spectrum spreads over many CTAs:
+//   1. mlp_max_kernel: cmax per sample (atomicMax on the bit patterns of non-negative floats,
+//      exact and independent of the order);
+//   2. mlp_binsum_kernel: one CTA per (segment, sample) sums log(max(c / cmax, 1e-30));
+//   3. mlp_binfin_kernel: per bin the segment sums in segment order, mean log + log cmax,
+//      the features.
+// log(max(c, 1e-30 cmax)) is evaluated as log(max(c/cmax, 1e-30)) + log(cmax) so that the floor
+// never underflows; one conversion to float per entry.  No floating-point atomics: the result
+// does not depend on the schedule.
+constexpr int kSegLen = 2048;
+
+__device__ __forceinline__ float block_sum256(float v, float* red8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red8[w];
+  return t;   // valid in thread 0
+}
+
+// cmax_bits[B] zeroed by the caller; grid (chunks, B)
+__global__ void __launch_bounds__(256) mlp_max_kernel(const double* __restrict__ chat, int K1,
+                                                      unsigned* __restrict__ cmax_bits) {
+  __shared__ float red8[8];
+  const double* c = chat + (size_t)blockIdx.y * K1;
   float mx = 0.f;
-  for (int i = threadIdx.x; i < K1; i += blockDim.x) mx = fmaxf(mx, (float)c[i]);
-  red[threadIdx.x] = mx;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K1; i += gridDim.x * blockDim.x) mx = fmaxf(mx, (float)c[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = mx;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = fmaxf(m, red8[w]);
+    if (!(m > 0.f)) m = 0.f;   // +0 (never -0 or NaN): bit patterns then order like the values
+    atomicMax(cmax_bits + blockIdx.y, __float_as_uint(m));
   }
-  const float cmax = red[0] > 0.f ? red[0] : 1.f;
-  const float inv = 1.f / cmax, lmax = logf(cmax);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int b = warp; b < kBins; b += nw) {
-    const uint32_t i0 = bin_start[b], i1 = bin_start[b + 1];
-    float acc = 0.f;
-    for (uint32_t i = i0 + lane; i < i1; i += 32) acc += logf(fmaxf((float)c[bin_order[i]] * inv, 1e-30f));
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) vals[b] = (i1 > i0) ? acc / (float)(i1 - i0) + lmax : 0.f;
-  }
+}
+
+__device__ __forceinline__ float cmax_of(const unsigned* cmax_bits, int smp) {
+  const float m = __uint_as_float(cmax_bits[smp]);
+  return m > 0.f ? m : 1.f;
+}
+
+// grid (nseg, B): part[smp][seg] = sum over the segment of log(max(c / cmax, 1e-30))
+__global__ void __launch_bounds__(256) mlp_binsum_kernel(const double* __restrict__ chat,
+                                                         const uint32_t* __restrict__ bin_order,
+                                                         const uint32_t* __restrict__ seg_off, int K1, int nseg,
+                                                         const unsigned* __restrict__ cmax_bits,
+                                                         float* __restrict__ part) {
+  __shared__ float red8[8];
+  const double* c = chat + (size_t)blockIdx.y * K1;
+  const float inv = 1.f / cmax_of(cmax_bits, blockIdx.y);
+  const uint32_t i0 = seg_off[blockIdx.x], i1 = seg_off[blockIdx.x + 1];
+  float acc = 0.f;
+  for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += logf(fmaxf((float)c[bin_order[i]] * inv, 1e-30f));
+  const float t = block_sum256(acc, red8);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * nseg + blockIdx.x] = t;
+}
+
+// grid B, kBins threads: per-bin means, their mean mu, features [binned - mu | centre_log]
+__global__ void __launch_bounds__(kBins) mlp_binfin_kernel(const float* __restrict__ part, int nseg,
+                                                           const uint32_t* __restrict__ bin_seg,
+                                                           const uint32_t* __restrict__ bin_start,
+                                                           const unsigned* __restrict__ cmax_bits,
+                                                           const float* __restrict__ centre_log,
+                                                           float* __restrict__ feat, float* __restrict__ mean) {
+  __shared__ float red4[kBins / 32];
+  const int b = threadIdx.x, smp = blockIdx.x;
+  const float lmax = logf(cmax_of(cmax_bits, smp));
+  const float* ps = part + (size_t)smp * nseg;
+  float acc = 0.f;
+  for (uint32_t sg = bin_seg[b]; sg < bin_seg[b + 1]; ++sg) acc += ps[sg];
+  const uint32_t n = bin_start[b + 1] - bin_start[b];
+  const float v = n ? acc / (float)n + lmax : 0.f;
+  float t = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((b & 31) == 0) red4[b >> 5] = t;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    float acc = 0.f;
-    for (int b = threadIdx.x; b < kBins; b += 32) acc += vals[b];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) mu_s = acc / kBins;
-  }
-  __syncthreads();
-  const float mu = mu_s;
-  float* f = feat + (size_t)blockIdx.x * kIn;
-  if (threadIdx.x < kBins) {
-    f[threadIdx.x] = vals[threadIdx.x] - mu;
-    f[kBins + threadIdx.x] = centre_log[threadIdx.x];
-  }
-  if (threadIdx.x == 0) mean[blockIdx.x] = mu;
+  float tot = 0.f;
+#pragma unroll
+  for (int w = 0; w < kBins / 32; ++w) tot += red4[w];
+  const float mu = tot / kBins;
+  float* f = feat + (size_t)smp * kIn;
+  f[b] = v - mu;
+  f[kBins + b] = centre_log[b];
+  if (b == 0) mean[smp] = mu;
 }
 
 // out_log: [128] learned binned log spectrum (mean already added); chat: [ny][L+1] f64
@@ -300,10 +349,25 @@ __global__ void mlp_adam_kernel(float* __restrict__ params, float* __restrict__ 
 int mlp_param_count() { return kParams; }
 int mlp_acts_per_sample() { return kActs; }
 
-cudaError_t launch_mlp_bin(const double* chat, const uint32_t* order, const uint32_t* start, const float* centre_log,
-                           int B, int K1, float* feat, float* mean, cudaStream_t s) {
-  mlp_bin_kernel<<<B, 256, 0, s>>>(chat, order, start, centre_log, K1, feat, mean);
-  return cudaGetLastError();
+int mlp_seg_len() { return kSegLen; }
+
+// Features of B spectra in slices of at most max_batch samples (the scratch: cmax_bits
+// [max_batch], part [max_batch][nseg]).
+cudaError_t launch_mlp_bin(const double* chat, const MlpBins& t, int B, float* feat, float* mean, cudaStream_t s) {
+  const int chunks = std::max(1, std::min((t.K1 + 4095) / 4096, 1024));
+  for (int b0 = 0; b0 < B; b0 += t.max_batch) {
+    const int nb = std::min(t.max_batch, B - b0);
+    const double* c = chat + (size_t)b0 * t.K1;
+    cudaError_t e = cudaMemsetAsync(t.cmax_bits, 0, nb * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    mlp_max_kernel<<<dim3(chunks, nb), 256, 0, s>>>(c, t.K1, t.cmax_bits);
+    mlp_binsum_kernel<<<dim3(t.nseg, nb), 256, 0, s>>>(c, t.order, t.seg_off, t.K1, t.nseg, t.cmax_bits, t.part);
+    mlp_binfin_kernel<<<nb, kBins, 0, s>>>(t.part, t.nseg, t.bin_seg, t.start, t.cmax_bits, t.centre_log,
+                                           feat + (size_t)b0 * kIn, mean + b0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_mlp_unbin(const float* out_log, int ny, int L, float w, double* chat, cudaStream_t s) {

@@ -1,4 +1,5 @@
 // C ABI of the learned spectral-variance denoiser.
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -9,8 +10,8 @@
 namespace fftenkf {
 void set_last_error(const std::string& msg);
 int mlp_param_count();
-cudaError_t launch_mlp_bin(const double* chat, const uint32_t* order, const uint32_t* start, const float* centre_log,
-                           int B, int K1, float* feat, float* mean, cudaStream_t s);
+int mlp_seg_len();
+cudaError_t launch_mlp_bin(const double* chat, const MlpBins& t, int B, float* feat, float* mean, cudaStream_t s);
 cudaError_t launch_mlp_finish(const float* out, const float* mean, float* out_log, int* flag, const double* chat_in,
                               double* chat_out, int K1, int ny, int L, float w, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float* params, const float* X, int B, float* out, float* acts, cudaStream_t s);
@@ -30,6 +31,7 @@ fftenkf_status mcuda(cudaError_t e, const char* where) {
   return e == cudaSuccess ? FFTENKF_OK : mfail(FFTENKF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 constexpr int kNB = 128;
+constexpr int kMaxBatch = 64;   // spectra binned per slice of a batch
 }  // namespace
 
 struct fftenkf_denoiser_s {
@@ -37,9 +39,16 @@ struct fftenkf_denoiser_s {
   float w;                 // bin width in |k| units
   uint32_t* d_order = nullptr;   // entries grouped by radial bin
   uint32_t* d_start = nullptr;   // [129] offsets of the bins in d_order
+  uint32_t* d_seg = nullptr;     // segment offsets [nseg + 1] | first segment of every bin [129]
+  int nseg = 0;
   float* d_centre_log = nullptr;
   float* d_scratch = nullptr;   // features 256 | mean 1 | out 128 | out_log 128
+  unsigned* d_cmax = nullptr;   // [kMaxBatch]
+  float* d_part = nullptr;      // [kMaxBatch][nseg]
   int* d_flag = nullptr;
+  MlpBins bins() const {
+    return MlpBins{K1, nseg, kMaxBatch, d_order, d_start, d_seg, d_seg + nseg + 1, d_centre_log, d_cmax, d_part};
+  }
 };
 
 extern "C" int fftenkf_mlp_param_count(void) { return mlp_param_count(); }
@@ -72,6 +81,16 @@ extern "C" fftenkf_status fftenkf_denoiser_create(fftenkf_denoiser* out, int ny,
   for (int b = 0; b < kNB; ++b) start[b + 1] += start[b];
   std::vector<uint32_t> order(d->K1), fill(start.begin(), start.end() - 1);
   for (int i = 0; i < d->K1; ++i) order[fill[bins[i]]++] = (uint32_t)i;
+  // every bin cut into segments of at most mlp_seg_len() entries
+  std::vector<uint32_t> seg(1, 0), bin_seg(kNB + 1, 0);
+  const uint32_t sl = (uint32_t)mlp_seg_len();
+  for (int b = 0; b < kNB; ++b) {
+    bin_seg[b] = (uint32_t)(seg.size() - 1);
+    for (uint32_t x = start[b]; x < start[b + 1]; x += sl) seg.push_back(std::min(x + sl, start[b + 1]));
+  }
+  bin_seg[kNB] = (uint32_t)(seg.size() - 1);
+  d->nseg = (int)(seg.size() - 1);
+  seg.insert(seg.end(), bin_seg.begin(), bin_seg.end());
   std::vector<float> cl(kNB);
   for (int b = 0; b < kNB; ++b) {
     const double c = (b + 0.5) * w;
@@ -81,6 +100,10 @@ extern "C" fftenkf_status fftenkf_denoiser_create(fftenkf_denoiser* out, int ny,
   if (e == cudaSuccess) e = cudaMemcpy(d->d_order, order.data(), d->K1 * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&d->d_start, (kNB + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemcpy(d->d_start, start.data(), (kNB + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_seg, seg.size() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_seg, seg.data(), seg.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_cmax, kMaxBatch * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_part, (size_t)kMaxBatch * std::max(d->nseg, 1) * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&d->d_centre_log, kNB * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(d->d_centre_log, cl.data(), kNB * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&d->d_scratch, (256 + 4 + 2 * kNB) * sizeof(float));
@@ -97,6 +120,9 @@ extern "C" fftenkf_status fftenkf_denoiser_destroy(fftenkf_denoiser d) {
   if (!d) return FFTENKF_OK;
   if (d->d_order) cudaFree(d->d_order);
   if (d->d_start) cudaFree(d->d_start);
+  if (d->d_seg) cudaFree(d->d_seg);
+  if (d->d_cmax) cudaFree(d->d_cmax);
+  if (d->d_part) cudaFree(d->d_part);
   if (d->d_centre_log) cudaFree(d->d_centre_log);
   if (d->d_scratch) cudaFree(d->d_scratch);
   if (d->d_flag) cudaFree(d->d_flag);
@@ -108,8 +134,7 @@ extern "C" fftenkf_status fftenkf_denoiser_features(fftenkf_denoiser d, const do
                                                     float* means, void* stream) {
   set_last_error("");
   if (!d || !chat || !features || !means || batch <= 0) return mfail(FFTENKF_EINVAL, "bad arguments");
-  return mcuda(launch_mlp_bin(chat, d->d_order, d->d_start, d->d_centre_log, batch, d->K1, features, means,
-                              static_cast<cudaStream_t>(stream)),
+  return mcuda(launch_mlp_bin(chat, d->bins(), batch, features, means, static_cast<cudaStream_t>(stream)),
                "denoiser_features");
 }
 
@@ -150,7 +175,7 @@ extern "C" fftenkf_status fftenkf_denoise_spectrum(fftenkf_denoiser d, const flo
   float* mean = feat + 256;
   float* out = mean + 4;
   float* out_log = out + kNB;
-  cudaError_t e = launch_mlp_bin(chat_in, d->d_order, d->d_start, d->d_centre_log, 1, d->K1, feat, mean, s);
+  cudaError_t e = launch_mlp_bin(chat_in, d->bins(), 1, feat, mean, s);
   if (e == cudaSuccess) e = launch_mlp_forward(params, feat, 1, out, nullptr, s);
   if (e == cudaSuccess)
     e = launch_mlp_finish(out, mean, out_log, d->d_flag, chat_in, chat_out, d->K1, d->ny, d->L, d->w, s);
