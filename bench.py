@@ -91,8 +91,7 @@ def pass_bytes(ny, nx, M, N, n_obs, s):
     n_un = M - n_obs
     nf = n_obs + 2 * n_obs * n_un     # floats per wavenumber of the covariance / gain tables
     return {
-        "mean": M * N * G * s + M * G * 4,
-        "row_fwd_anomaly": M * N * G * s + M * G * 4 + M * N * line,
+        "row_fwd_anomaly": M * N * G * s + M * N * line,   # members in (pivot rows re-read through L2), rows out
         "rhat_transpose": 2 * n_obs * K1 * 8,
         "col_stats": M * N * line + n_obs * K1 * 8 + nf * K1 * 4,      # rows in, rhat in, gains out
         "gain": nf * K1 * 4 + n_obs * K1 * 8 + nf * K1 * 4,            # caller-spectrum analyses only

@@ -1,9 +1,9 @@
 // C ABI: plans, argument validation and the order of the passes.
 //
 // analyze (Sec. 2.1, eq. spectral-multi-enkf), on the caller's stream unless noted:
-//   0. rhat_transpose  rhat to the column layout            [auxiliary stream, overlaps 1-2]
-//   1. mean            ubar^(j) over members                          (eq. dii)
-//   2. row_fwd anomaly  rows of F(u_k^(j) - ubar^(j)) -> A
+//   0. rhat_transpose  rhat to the column layout            [auxiliary stream, overlaps 2]
+//   2. row_fwd anomaly  rows of F(u_k^(j) - u_0^(j)), k >= 1, and of sqrt(N) F(ubar^(j) - u_0^(j))
+//                      in the place of k = 0 -> A (first member as pivot: no mean pass)
 //   3. col_stats       columns of F, chat^(oo), chat^(jo) and the gains
 //                      chat/(chat^(oo)+rhat) -> goo, gjo (eq. dii, cov-multi-spectral, spectral-multi-enkf)
 //   5. row_fwd innov   rows of F(d_o + e_{k,o} - u_k^(o)) -> W
@@ -27,6 +27,8 @@
 
 using namespace fftenkf;
 
+// kPassMean: the retired mean pass (the anomaly rows take the first member as pivot); its slot
+// keeps the later indices stable and its time reads 0
 enum Pass { kPassMean, kPassRowAnom, kPassStats, kPassGain, kPassRowInnov, kPassUpdate, kPassRowInv,
             kPassChatOut, kPassRhatT, kPassFused, kPassCount };
 static const char* kPassNames[kPassCount] = {"mean", "row_fwd_anomaly", "col_stats", "gain",
@@ -74,7 +76,7 @@ struct fftenkf_plan_s {
   bool tm_ok = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // workspace layout (byte offsets)
-  size_t off_mean, off_A, off_W, off_chat, off_goo, off_gjo, off_rhat_t, off_amp, ws_bytes;
+  size_t off_A, off_W, off_chat, off_goo, off_gjo, off_rhat_t, off_amp, ws_bytes;
   void* own_ws = nullptr;
   int device = 0;
   // per-pass CUDA-event timing (fftenkf_set_profiling); a ring of event pairs per pass
@@ -148,7 +150,6 @@ static void layout(fftenkf_plan_s* p) {
   const size_t tab = (size_t)(p->L + 1) * p->ny;
   const size_t gain_tables = p->coupled ? (size_t)p->M * p->n_obs : (size_t)p->n_obs * p->n_un;
   size_t off = 0;
-  p->off_mean = off; off = round_up(off + (size_t)p->M * G * sizeof(float), 256);
   p->off_A = off;    off = round_up(off + (size_t)p->M * p->N * line, 256);
   p->off_chat = off; off = round_up(off + (size_t)table_floats(p) * tab * sizeof(float), 256);
   p->off_W = off;    off = round_up(off + (size_t)p->N * p->n_obs * line, 256);
@@ -309,42 +310,35 @@ static ColFusedParams fused_params(fftenkf_plan p, char* ws) {
   return f;
 }
 
-// steps 1-3: mean, anomaly row spectra, column statistics -> chat_t
-// with rhat_t != null the column pass also forms the gains (analysis) and skips chat_t
-static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s, const double* rhat_t,
-                                  cudaEvent_t wait_before_stats = nullptr) {
-  MeanParams mp;
-  mp.M = p->M;
-  mp.N = p->N;
-  mp.storage = p->storage;
-  mp.G = (long long)p->ny * p->nx;
-  mp.ens = ens;
-  mp.mean = reinterpret_cast<float*>(ws + p->off_mean);
-  mp.status = p->d_status;
-  mp.vsel = p->sched[kPassMean];
-  prof_begin(p, kPassMean, s);
-  cudaError_t e = launch_mean(mp, s);
-  prof_end(p, kPassMean, s);
-  if (e != cudaSuccess) return e;
+// step 2: anomaly row spectra (pivot form) -> A
+static cudaError_t run_anomaly_rows(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s) {
   RowFwdParams rp;
   memset(&rp, 0, sizeof(rp));
   rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
   rp.n_obs = p->n_obs; rp.mode = kAnomaly; rp.storage = p->storage;
-  rp.ens = ens; rp.mean = mp.mean;
+  rp.ens = ens;
   rp.out = reinterpret_cast<float2*>(ws + p->off_A);
   rp.vsel = p->sched[kPassRowAnom];
   rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
   rp.expire_first_wait = p->expire_first_wait;
   prof_begin(p, kPassRowAnom, s);
-  e = launch_row_fwd(rp, p->M * p->N, s);
+  cudaError_t e = launch_row_fwd(rp, p->M * p->N, s);
   prof_end(p, kPassRowAnom, s);
+  return e;
+}
+
+// steps 2-3: anomaly row spectra, column statistics -> chat_t
+// with rhat_t != null the column pass also forms the gains (analysis) and skips chat_t
+static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s, const double* rhat_t,
+                                  cudaEvent_t wait_before_stats = nullptr) {
+  cudaError_t e = run_anomaly_rows(p, ens, ws, s);
   if (e != cudaSuccess) return e;
   ColStatsParams cp;
   memset(&cp, 0, sizeof(cp));
   cp.ny = p->ny; cp.L = p->L; cp.M = p->M; cp.N = p->N; cp.n_obs = p->n_obs; cp.n_un = p->n_un;
   for (int i = 0; i < p->n_obs; ++i) cp.obs[i] = p->obs[i];
   for (int u = 0; u < p->n_un; ++u) cp.un[u] = p->un[u];
-  cp.A = rp.out;
+  cp.A = reinterpret_cast<const float2*>(ws + p->off_A);
   cp.chat = rhat_t ? nullptr : reinterpret_cast<float*>(ws + p->off_chat);
   cp.rhat_t = rhat_t;
   cp.goo = reinterpret_cast<float*>(ws + p->off_goo);
@@ -370,36 +364,6 @@ static cudaError_t run_statistics(fftenkf_plan p, const void* ens, char* ws, cud
   prof_begin(p, kPassStats, s);
   e = launch_col_stats(cp, s);
   prof_end(p, kPassStats, s);
-  return e;
-}
-
-// steps 1-2 only (the fused path transforms the columns later)
-static cudaError_t run_mean_rows(fftenkf_plan p, const void* ens, char* ws, cudaStream_t s) {
-  MeanParams mp;
-  mp.M = p->M;
-  mp.N = p->N;
-  mp.storage = p->storage;
-  mp.G = (long long)p->ny * p->nx;
-  mp.ens = ens;
-  mp.mean = reinterpret_cast<float*>(ws + p->off_mean);
-  mp.status = p->d_status;
-  mp.vsel = p->sched[kPassMean];
-  prof_begin(p, kPassMean, s);
-  cudaError_t e = launch_mean(mp, s);
-  prof_end(p, kPassMean, s);
-  if (e != cudaSuccess) return e;
-  RowFwdParams rp;
-  memset(&rp, 0, sizeof(rp));
-  rp.ny = p->ny; rp.nx = p->nx; rp.L = p->L; rp.M = p->M; rp.N = p->N;
-  rp.n_obs = p->n_obs; rp.mode = kAnomaly; rp.storage = p->storage;
-  rp.ens = ens; rp.mean = mp.mean;
-  rp.out = reinterpret_cast<float2*>(ws + p->off_A);
-  rp.vsel = p->sched[kPassRowAnom];
-  rp.twL = p->twL(rp.vsel & 1); rp.twX = p->twX(); rp.status = p->d_status;
-  rp.expire_first_wait = p->expire_first_wait;
-  prof_begin(p, kPassRowAnom, s);
-  e = launch_row_fwd(rp, p->M * p->N, s);
-  prof_end(p, kPassRowAnom, s);
   return e;
 }
 
@@ -476,8 +440,8 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
   }
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
   if (fused) {
-    // mean and anomaly rows now; the columns after the innovation rows
-    if (e == cudaSuccess) e = run_mean_rows(p, ensemble, ws, s);
+    // anomaly rows now; the columns after the innovation rows
+    if (e == cudaSuccess) e = run_anomaly_rows(p, ensemble, ws, s);
   } else if (!spectrum && p->coupled) {
     // tables of the column statistics, then the coupled gains (FP64 bracket inverse per wavenumber)
     if (e == cudaSuccess) e = run_statistics(p, ensemble, ws, s, nullptr);
@@ -494,7 +458,7 @@ static fftenkf_status analyze_impl(fftenkf_plan p, void* ensemble, const float* 
     if (e == cudaSuccess) e = launch_coupled_gain(cg, s);
     prof_end(p, kPassGain, s);
   } else if (!spectrum) {
-    // mean and anomaly rows need no rhat; the statistics pass (which forms the gains) waits for it
+    // anomaly rows need no rhat; the statistics pass (which forms the gains) waits for it
     if (e == cudaSuccess) e = run_statistics(p, ensemble, ws, s, rhat_t, p->ev_join);
   } else {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);

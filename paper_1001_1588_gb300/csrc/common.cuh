@@ -78,22 +78,12 @@ __device__ __forceinline__ void store2(void* base, size_t idx, float2 v, int sto
   }
 }
 
-struct MeanParams {
-  int M, N, storage;
-  long long G;            // grid points per field
-  const void* ens;        // [M][N][G]
-  float* mean;            // [M][G]
-  int* status;            // device status word (bounded waits of the staged kernel), or null
-  int vsel;               // schedule: 0 = 2 stages of 2048 points, 1 = 4 stages of 1024 points
-};
-
 struct RowFwdParams {
   int ny, nx, L, R;       // L = nx/2, R rows per CTA
   int M, N, n_obs, mode, storage;
   int n_tiles;            // ny / R
   int obs[kMaxObs];
   const void* ens;        // [M][N][ny][nx]
-  const float* mean;      // [M][ny][nx]         (anomaly mode)
   const float* data;      // [n_obs][ny][nx]     (innovation mode)
   const void* pert;       // [N][n_obs][ny][nx]  (innovation mode)
   float2* out;            // row spectra: anomaly field j*N+k, innovation field k*n_obs+i
@@ -102,6 +92,9 @@ struct RowFwdParams {
   int* status;
   int vsel;               // line-FFT schedule (plan_V)
   int expire_first_wait;  // test setting: every CTA's first bulk-copy wait gives up at once
+  // anomaly mode: 1/sqrt(N), and the tensor-memory columns of the running sums (set by the launcher)
+  float inv_sqrt_N;
+  int tm_cols, tm_alloc;  // per thread (a multiple of 8), per CTA (a power of two >= 32)
 };
 
 struct RowInvParams {
@@ -211,7 +204,6 @@ struct GainParams {
 };
 
 // host-side launchers (one switch over the line length per pass)
-cudaError_t launch_mean(const MeanParams& p, cudaStream_t s);
 cudaError_t launch_row_fwd(const RowFwdParams& p, int n_fields, cudaStream_t s);
 cudaError_t launch_row_inv(const RowInvParams& p, int n_fields, cudaStream_t s);
 // rows per item of the inverse row pass for (nx/2, schedule, ny, nx, storage bytes); 0 = unsupported

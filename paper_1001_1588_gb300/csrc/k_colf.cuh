@@ -103,9 +103,11 @@ __device__ __forceinline__ void store_halves(const cp (&v)[V], uint32_t at) {
 // Statistics of one transformed pair (roles 2pp, 2pp+1) into the tensor-memory sums at ta:
 // auto sums of observed role i at columns [i V, i V + V), cross sums of unobserved u with
 // observed i at XB + (u n_obs + i) 2V, interleaved (re, im) per wavenumber.  The observed
-// spectra of the member (half i of its first pair) are at KB + 2 V i.
+// spectra of the member (half i of its first pair) are at KB + 2 V i.  sg = -1 subtracts the
+// products (the pivot sum in the place of member 0), +1 adds them.
 template <int V, int NOBS>
-__device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M, int n_obs, uint32_t ta, int KB) {
+__device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M, int n_obs, uint32_t ta, int KB,
+                                                 float sg) {
   const int XB = n_obs * V;
   tm_wait_st();   // the sums (and the member's spectra) stored by earlier units
 #pragma unroll
@@ -118,7 +120,7 @@ __device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M
 #pragma unroll
       for (int m = 0; m < V; ++m) {
         const float2 x = h ? half_of<1>(v[m]) : half_of<0>(v[m]);
-        a[m] = fmaf(x.x, x.x, fmaf(x.y, x.y, a[m]));
+        a[m] = fmaf(sg * x.x, x.x, fmaf(sg * x.y, x.y, a[m]));
       }
       tm_st<V>(ta + r * V, a);
     } else {
@@ -131,8 +133,9 @@ __device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M
         tm_ld<2 * V>(at, a);
         tm_ld<2 * V>(ta + KB + 2 * V * i, o);
 #pragma unroll
-        for (int m = 0; m < V; ++m) {   // += x conj(o)
-          const float2 x = h ? half_of<1>(v[m]) : half_of<0>(v[m]);
+        for (int m = 0; m < V; ++m) {   // += sg x conj(o)
+          float2 x = h ? half_of<1>(v[m]) : half_of<0>(v[m]);
+          x = make_float2(sg * x.x, sg * x.y);
           a[2 * m] = fmaf(x.x, o[2 * m], fmaf(x.y, o[2 * m + 1], a[2 * m]));
           a[2 * m + 1] = fmaf(x.y, o[2 * m], fmaf(-x.x, o[2 * m + 1], a[2 * m + 1]));
         }
@@ -145,8 +148,10 @@ __device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M
 // Sums -> gains in place (analysis), or -> covariance tables in global memory (statistics
 // only), for the wavenumbers (t + T m, column c) of this thread.  The denominator
 // chat^(oo) + rhat is formed in FP64 and rounded once; the quotients are FP32, or FP64 where
-// the rounded denominator is below FLT_MIN (0 where it is 0).  Returns false if a sum is
-// not finite.
+// the rounded denominator is below FLT_MIN (0 where it is exactly 0, as in the oracle).  With
+// the pivot form chat^(oo) can come out a few rounding errors below 0 where the ensemble has
+// no variance above FFT round-off; with rhat = 0 such a wavenumber keeps the gain 1 of
+// chat / chat.  Returns false if a sum is not finite.
 template <int NY, int V, int NOBS>
 __device__ __forceinline__ bool fused_gains(const ColFusedParams& p, uint32_t ta, int c, int t) {
   constexpr int T = NY / V;
@@ -184,7 +189,7 @@ __device__ __forceinline__ bool fused_gains(const ColFusedParams& p, uint32_t ta
           a[m] = val[m] * inv[m];
         } else {
           tiny |= 1u << m;
-          const double rd = (den > 0.0) ? (double)p.inv_G / den : 0.0;
+          const double rd = (den != 0.0) ? (double)p.inv_G / den : 0.0;
           inv[m] = 0.f;
           a[m] = (float)((double)val[m] * rd);
         }
@@ -204,7 +209,7 @@ __device__ __forceinline__ bool fused_gains(const ColFusedParams& p, uint32_t ta
           xout[(size_t)(i * p.n_un + u) * tab + (size_t)c * NY + t + T * m] = make_float2(xr, xi);
         } else if (tiny & (1u << m)) {
           const double den = (double)val[m] + rr[m];
-          const double rd = (den > 0.0) ? (double)p.inv_G / den : 0.0;
+          const double rd = (den != 0.0) ? (double)p.inv_G / den : 0.0;
           x[2 * m] = (float)((double)xr * rd);
           x[2 * m + 1] = (float)((double)xi * rd);
         } else {
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(V <= 8 ? 512 : 256, 1) col_fused_kernel(const 
         // the exchange buffer is next written after the next unit's barriers
         fft_pair<NY, V, false, false>(v, xbuf, t, p.tw, bid);
         if (pp == 0) store_halves<V>(v, ta + KB);
-        fused_accumulate<V, NOBS>(v, pp, M, p.n_obs, ta, KB);
+        fused_accumulate<V, NOBS>(v, pp, M, p.n_obs, ta, KB, u < P ? -1.f : 1.f);   // units of member 0 first
         if (u == units_stats - 1) bad |= !fused_gains<NY, V, NOBS>(p, ta, c, t);
       } else {
         const int k = u - units_stats;

@@ -24,7 +24,8 @@
 namespace fftenkf {
 
 // Gains of one wavenumber whose denominator chat^(oo) + rhat is below FLT_MIN (both
-// vanish): the quotients in FP64, 0 where the denominator is 0.  Kept out of line so
+// vanish, or rhat = 0 and chat a few rounding errors below 0): the quotients in FP64, 0
+// where the denominator is exactly 0.  Kept out of line so
 // that the common FP32 path carries none of its instructions.  xa: the first cross
 // accumulator of this wavenumber (stride ny between tables).  Returns false if a
 // cross spectrum is not finite.
@@ -32,7 +33,7 @@ static __device__ __noinline__ bool gains_fp64(float* goo, float2* gjo, float2* 
                                         int i, int n_un, size_t at, size_t tab, double den, float val, float inv_G,
                                         float scale) {
   bool ok = true;
-  const double rd = (den > 0.0) ? (double)inv_G / den : 0.0;
+  const double rd = (den != 0.0) ? (double)inv_G / den : 0.0;
   goo[i * tab + at] = (float)((double)val * rd);
   for (int u = 0; u < n_un; ++u) {
     const float2 a = xa[(size_t)(i * n_un + u) * xstride];
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
       for (int m = 0; m < V; ++m) ko[i][m] = make_float2(0.f, 0.f);
     for (int l = 0; l < lines_per_col; ++l) {
       const int b = l % M;
+      const float sg = (l < M) ? -1.f : 1.f;   // member 0's place holds the pivot sum: its products are subtracted
       if (!cta_wait(bar, phase, p.status, flag)) return;
       phase ^= 1;
       float2 v[V];
@@ -142,15 +144,16 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
             for (int m = 0; m < V; ++m) {
               ko[i][m] = v[m];
               float& a = acc[i * NY + t + T * m];
-              a = fmaf(v[m].x, v[m].x, fmaf(v[m].y, v[m].y, a));
+              a = fmaf(sg * v[m].x, v[m].x, fmaf(sg * v[m].y, v[m].y, a));
             }
             if (NOBS >= 2 && i == 1 && p.n_pair) {   // coupled: observed pair chat^(o1 o0) += v conj(ko_0)
               float2* a = xacc + t;
 #pragma unroll
               for (int m = 0; m < V; ++m) {
+                const float2 w = make_float2(sg * v[m].x, sg * v[m].y);
                 float2 o = a[T * m];
-                o.x = fmaf(v[m].x, ko[0][m].x, fmaf(v[m].y, ko[0][m].y, o.x));
-                o.y = fmaf(v[m].y, ko[0][m].x, fmaf(-v[m].x, ko[0][m].y, o.y));
+                o.x = fmaf(w.x, ko[0][m].x, fmaf(w.y, ko[0][m].y, o.x));
+                o.y = fmaf(w.y, ko[0][m].x, fmaf(-w.x, ko[0][m].y, o.y));
                 a[T * m] = o;
               }
             }
@@ -164,10 +167,11 @@ __global__ void __launch_bounds__((NY / V > 256) ? 512 : 256, 1) col_stats_kerne
             float2* a = xacc + (size_t)(p.n_pair + i * p.n_un + u) * NY + t;
 #pragma unroll
             for (int m = 0; m < V; ++m) {
-              // o += v conj(ko), as two fused multiply-adds per component
+              // o += sg v conj(ko), as two fused multiply-adds per component
+              const float2 w = make_float2(sg * v[m].x, sg * v[m].y);
               float2 o = a[T * m];
-              o.x = fmaf(v[m].x, ko[i][m].x, fmaf(v[m].y, ko[i][m].y, o.x));
-              o.y = fmaf(v[m].y, ko[i][m].x, fmaf(-v[m].x, ko[i][m].y, o.y));
+              o.x = fmaf(w.x, ko[i][m].x, fmaf(w.y, ko[i][m].y, o.x));
+              o.y = fmaf(w.y, ko[i][m].x, fmaf(-w.x, ko[i][m].y, o.y));
               a[T * m] = o;
             }
           }

@@ -11,9 +11,22 @@
 // so that the column passes read each wavenumber column as one contiguous line.
 // The inverse row pass does the same in reverse and adds the increment to the
 // forecast member in the same pass.
+//
+// The anomaly rows take the first member as pivot (row_anom_kernel): the sample
+// covariance of eq. (dii) is unchanged when one field is subtracted from every
+// member, and d_k = u_k - u_0 is exact in FP32 for BF16 members (and for FP32
+// members within a factor two of each other, as under a large common mean), so
+// the transforms see anomaly-sized values and no mean pass is needed.  Field
+// j*N+k (k >= 1) receives the row spectra of d_k; field j*N+0 receives those of
+// (1/sqrt N) sum_k d_k = sqrt(N) (ubar - u_0), whose products the column
+// statistics subtract: sum_k D_k D'_k* - N Dbar Dbar'* = sum_k A_k A'_k* with
+// D = F d, Dbar = F(ubar - u_0), A_k = F(u_k - ubar).
 #pragma once
+#include <cmath>
+
 #include "common.cuh"
 #include "tma.cuh"
+#include "tmem.cuh"
 
 namespace fftenkf {
 
@@ -23,11 +36,10 @@ int sm_count();
   X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048) X(3072) X(4096)
 
 // ----------------------------------------------------------------- rows
-// Persistent CTAs walk the tiles (member fastest, so the CTAs working on the
-// same rows of different members run together and share the mean or data rows
-// through L2).  Each tile of R rows is done in rounds of LPC rows; the
-// per-member input rows of the next round (u, and e for innovations) are bulk
-// copied into a shared-memory stage while the current round is transformed.
+// Persistent CTAs walk the tiles.  Each tile of R rows is done in rounds of LPC
+// rows; the per-member input rows of the next round (u, and e for innovations)
+// are bulk copied into a shared-memory stage while the current round is
+// transformed.
 struct RowTile {
   int k, tile, jb;
 };
@@ -41,6 +53,48 @@ __device__ __forceinline__ RowTile decode_tile(long long q, int N, int n_tiles) 
   return r;
 }
 
+// Spectrum of the R real rows staged in `lines` (their L-point transforms), written transposed:
+// out[c][y0 + r] of the field at fout.  Columns c and L - c come from the same pair Z[c], Z[L-c]:
+// with E = (Z[c] + conj Z[L-c]) / 2 and O = -i (Z[c] - conj Z[L-c]) / 2, X[c] = E + W^c O and
+// X[L-c] = conj(E - W^c O); column 0 holds X[0] + i X[L] (packed).  Every thread of the CTA calls it.
+template <int L>
+__device__ __forceinline__ void row_twist_store(const float2* lines, float2* fout, int R, int ny, int y0,
+                                                const float2* __restrict__ twX) {
+  constexpr int pitch = row_pitch(L);
+  const int RP = R >> 1;
+  const int rp = threadIdx.x % RP;
+  const int cstep = blockDim.x / RP;
+  float2* out = fout + y0 + 2 * rp;
+  const float2* r0 = lines + (2 * rp) * pitch;
+  const float2* r1 = r0 + pitch;
+  for (int c = threadIdx.x / RP; c <= L / 2; c += cstep) {
+    const float2 Z0 = r0[pidx(c)], Z1 = r1[pidx(c)];
+    if (c == 0) {
+      *reinterpret_cast<float4*>(out) = make_float4(Z0.x + Z0.y, Z0.x - Z0.y, Z1.x + Z1.y, Z1.x - Z1.y);
+      continue;
+    }
+    const float2 C0 = r0[pidx(L - c)], C1 = r1[pidx(L - c)];
+    float2 wt = __ldg(twX + c);
+    wt = make_float2(0.5f * wt.x, 0.5f * wt.y);
+    float2 lo[2], hi[2];
+    const float2 Zs[2] = {Z0, Z1}, Cs[2] = {C0, C1};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float2 E2 = make_float2(Zs[h].x + Cs[h].x, Zs[h].y - Cs[h].y);   // 2 E
+      const float2 O2 = make_float2(Zs[h].y + Cs[h].y, Cs[h].x - Zs[h].x);   // 2 O
+      const float2 P = cmul(wt, O2);                                          // W^c O
+      lo[h] = make_float2(fmaf(0.5f, E2.x, P.x), fmaf(0.5f, E2.y, P.y));
+      hi[h] = make_float2(fmaf(0.5f, E2.x, -P.x), fmaf(-0.5f, E2.y, P.y));
+    }
+    *reinterpret_cast<float4*>(out + (size_t)c * ny) = make_float4(lo[0].x, lo[0].y, lo[1].x, lo[1].y);
+    if (c != L - c)
+      *reinterpret_cast<float4*>(out + (size_t)(L - c) * ny) = make_float4(hi[0].x, hi[0].y, hi[1].x, hi[1].y);
+  }
+}
+
+// Innovation rows: work items (member k fastest, tile, observed block), so that the CTAs
+// working on the same rows of different members run together and share the data rows
+// through L2.
 template <int L, int V, int ST, int MODE>
 __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   constexpr int T = L / V;
@@ -59,20 +113,18 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   unsigned char* stage = smraw + (((size_t)p.R * pitch * sizeof(float2) + 127) & ~(size_t)127);
   uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)n_in * round_bytes);
   int* flag = reinterpret_cast<int*>(bar + 1);
-  const int n_jb = (MODE == kAnomaly) ? p.M : p.n_obs;
-  const long long Q = (long long)n_jb * p.n_tiles * p.N;
+  static_assert(MODE != kAnomaly, "anomaly rows: row_anom_kernel");
+  const long long Q = (long long)p.n_obs * p.n_tiles * p.N;
   const char* ens = reinterpret_cast<const char*>(p.ens);
   const char* pert = reinterpret_cast<const char*>(p.pert);
 
   auto issue = [&](long long q, int r) {
     const RowTile w = decode_tile(q, p.N, p.n_tiles);
     const size_t row0 = (size_t)w.tile * p.R + (size_t)r * LPC;
-    int blk = w.jb;                 // anomaly: block jb; innovation: the jb-th observed block
-    if constexpr (MODE != kAnomaly) {
+    int blk = w.jb;                 // the jb-th observed block
 #pragma unroll
-      for (int i = 0; i < kMaxObs; ++i)   // constant indices: the parameter array stays in the constant bank
-        if (i == w.jb) blk = p.obs[i];
-    }
+    for (int i = 0; i < kMaxObs; ++i)   // constant indices: the parameter array stays in the constant bank
+      if (i == w.jb) blk = p.obs[i];
     const size_t fu = (size_t)blk * p.N + w.k;
     mbar_arrive_expect_tx(bar, n_in * round_bytes);
     bulk_g2s(stage, ens + (fu * G + row0 * nx) * es, round_bytes, bar);
@@ -90,15 +142,12 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
   uint32_t phase = 0;
   long long q = blockIdx.x;
   if (threadIdx.x == 0 && q < Q) issue(q, 0);
-  const int RP = p.R >> 1;
-  const int rp = threadIdx.x % RP;
-  const int cstep = blockDim.x / RP;
   bool expire = p.expire_first_wait != 0;   // test setting: the CTA's first wait gives up
   for (; q < Q; q += gridDim.x) {
     const RowTile w = decode_tile(q, p.N, p.n_tiles);
     const int y0 = w.tile * p.R;
-    const size_t f = (MODE == kAnomaly) ? (size_t)w.jb * p.N + w.k : (size_t)w.k * p.n_obs + w.jb;
-    const float* shared_in = (MODE == kAnomaly) ? p.mean + (size_t)w.jb * G : p.data + (size_t)w.jb * G;
+    const size_t f = (size_t)w.k * p.n_obs + w.jb;
+    const float* shared_in = p.data + (size_t)w.jb * G;
     for (int r = 0; r < rounds; ++r) {
       const int row = r * LPC + g;
       const float* sh = shared_in + (size_t)(y0 + row) * nx;
@@ -114,9 +163,7 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
       for (int m = 0; m < V; ++m) {
         const size_t idx = 2 * (size_t)(t + T * m);
         const float2 a = load2<ST>(st_row, idx);
-        if constexpr (MODE == kAnomaly) {
-          v[m] = make_float2(a.x - sv[m].x, a.y - sv[m].y);
-        } else if constexpr (MODE == kInnovation) {
+        if constexpr (MODE == kInnovation) {
           const float2 ee = load2<ST>(st_row + round_bytes, idx);
           // w = (d - u) + e: d - u first, exact when d and u are close (large common mean)
           v[m] = make_float2((sv[m].x - a.x) + ee.x, (sv[m].y - a.y) + ee.y);
@@ -135,37 +182,156 @@ __global__ void __launch_bounds__(512, 1) row_fwd_kernel(const RowFwdParams p) {
       for (int m = 0; m < V; ++m) line[pidx(t + T * m)] = v[m];
     }
     __syncthreads();
-    // spectrum of the real rows, written transposed: out[c][y0 + r].  Columns c and L - c
-    // come from the same pair Z[c], Z[L-c]: with E = (Z[c] + conj Z[L-c]) / 2 and
-    // O = -i (Z[c] - conj Z[L-c]) / 2, X[c] = E + W^c O and X[L-c] = conj(E - W^c O).
-    float2* out = p.out + f * (size_t)L * p.ny + y0 + 2 * rp;
-    const float2* r0 = lines + (2 * rp) * pitch;
-    const float2* r1 = r0 + pitch;
-    for (int c = threadIdx.x / RP; c <= L / 2; c += cstep) {
-      const float2 Z0 = r0[pidx(c)], Z1 = r1[pidx(c)];
-      if (c == 0) {   // packed: X[0] + i X[L]
-        *reinterpret_cast<float4*>(out) = make_float4(Z0.x + Z0.y, Z0.x - Z0.y, Z1.x + Z1.y, Z1.x - Z1.y);
-        continue;
-      }
-      const float2 C0 = r0[pidx(L - c)], C1 = r1[pidx(L - c)];
-      float2 wt = __ldg(p.twX + c);
-      wt = make_float2(0.5f * wt.x, 0.5f * wt.y);
-      float2 lo[2], hi[2];
-      const float2 Zs[2] = {Z0, Z1}, Cs[2] = {C0, C1};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float2 E2 = make_float2(Zs[h].x + Cs[h].x, Zs[h].y - Cs[h].y);   // 2 E
-        const float2 O2 = make_float2(Zs[h].y + Cs[h].y, Cs[h].x - Zs[h].x);   // 2 O
-        const float2 P = cmul(wt, O2);                                          // W^c O
-        lo[h] = make_float2(fmaf(0.5f, E2.x, P.x), fmaf(0.5f, E2.y, P.y));
-        hi[h] = make_float2(fmaf(0.5f, E2.x, -P.x), fmaf(-0.5f, E2.y, P.y));
-      }
-      *reinterpret_cast<float4*>(out + (size_t)c * p.ny) = make_float4(lo[0].x, lo[0].y, lo[1].x, lo[1].y);
-      if (c != L - c)
-        *reinterpret_cast<float4*>(out + (size_t)(L - c) * p.ny) = make_float4(hi[0].x, hi[0].y, hi[1].x, hi[1].y);
-    }
+    row_twist_store<L>(lines, p.out + f * (size_t)L * p.ny, p.R, p.ny, y0, p.twX);
     __syncthreads();
   }
+}
+
+// Anomaly rows with the first member as pivot.  A work item is R rows of one block j; the CTA
+// takes its members k = 1..N-1 in turn (rounds of LPC rows each, the next round's rows bulk
+// copied while the current one is transformed), transforms d_k = u_k - u_0 into field j*N+k, and
+// keeps the running sum of the d_k of its rows: thread (g, t) the 2V values of each round, in
+// tm_cols tensor-memory columns of its lane -- or, for CTAs that are not whole warps (short
+// rows; tm_alloc == 0), in a shared-memory slot of tm_cols floats.  A last step transforms that
+// sum times 1/sqrt(N) into field j*N+0.  The pivot rows are read from global memory (L1/L2)
+// next to every round.
+template <int L, int V, int ST>
+__global__ void __launch_bounds__(512, 1) row_anom_kernel(const RowFwdParams p) {
+  constexpr int T = L / V;
+  constexpr int pitch = row_pitch(L);
+  static_assert((2 * V) % 8 == 0, "tensor-memory runs of 8 columns");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int LPC = blockDim.x / T;
+  const int rounds = p.R / LPC;
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x - g * T;
+  const int nx = p.nx, N = p.N;
+  const size_t G = (size_t)p.ny * nx;
+  constexpr int es = (ST == kBF16) ? 2 : 4;
+  const uint32_t round_bytes = (uint32_t)LPC * nx * es;
+  float2* lines = reinterpret_cast<float2*>(smraw);
+  unsigned char* stage = smraw + (((size_t)p.R * pitch * sizeof(float2) + 127) & ~(size_t)127);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + round_bytes);
+  int* flag = reinterpret_cast<int*>(bar + 1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(flag + 1);
+  const bool in_tm = p.tm_alloc != 0;
+  float* ssum = reinterpret_cast<float*>(tslot + 1) + (size_t)threadIdx.x * p.tm_cols;   // !in_tm
+  const long long Q = (long long)p.M * p.n_tiles;   // item q: block q / n_tiles, tile q mod n_tiles
+  const int steps = (N - 1) * rounds;              // copy unit s of an item: member 1 + s / rounds, round s mod rounds
+  const char* ens = reinterpret_cast<const char*>(p.ens);
+
+  auto issue = [&](long long q, int s) {
+    const int jb = (int)(q / p.n_tiles);
+    const int tile = (int)(q - (long long)jb * p.n_tiles);
+    const int k = 1 + s / rounds, r = s - (s / rounds) * rounds;
+    const size_t row0 = (size_t)tile * p.R + (size_t)r * LPC;
+    mbar_arrive_expect_tx(bar, round_bytes);
+    bulk_g2s(stage, ens + (((size_t)jb * N + k) * G + row0 * nx) * es, round_bytes, bar);
+  };
+
+  if (in_tm && (threadIdx.x >> 5) == 0) tm_alloc(tslot, (uint32_t)p.tm_alloc);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  if (in_tm) tm_fence_before_sync();
+  __syncthreads();
+  if (in_tm) tm_fence_after_sync();
+  const uint32_t ta = in_tm ? tm_addr(*tslot, (threadIdx.x >> 7) * p.tm_cols) : 0u;
+  auto sum_load = [&](int r, float* acc) {
+    if (in_tm) {
+      tm_wait_st();   // this thread's earlier stores
+      tm_ld<2 * V>(ta + (uint32_t)(r * 2 * V), acc);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 2 * V; ++i) acc[i] = ssum[r * 2 * V + i];
+    }
+  };
+  auto sum_store = [&](int r, const float* acc) {
+    if (in_tm) {
+      tm_st<2 * V>(ta + (uint32_t)(r * 2 * V), acc);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 2 * V; ++i) ssum[r * 2 * V + i] = acc[i];
+    }
+  };
+
+  uint32_t phase = 0;
+  long long q = blockIdx.x;
+  if (threadIdx.x == 0 && q < Q) issue(q, 0);
+  bool expire = p.expire_first_wait != 0;   // test setting: the CTA's first wait gives up
+  bool alive = true;
+  for (; q < Q && alive; q += gridDim.x) {
+    const int jb = (int)(q / p.n_tiles);
+    const int y0 = (int)(q - (long long)jb * p.n_tiles) * p.R;
+    const char* piv = ens + (size_t)jb * N * G * es;   // member 0 of block j
+    for (int k = 1; k <= N && alive; ++k) {   // k == N: the scaled sum, written as member 0
+      for (int r = 0; r < rounds; ++r) {
+        const int row = r * LPC + g;
+        float2 v[V];
+        if (k < N) {
+          float2 sv[V];
+          const char* prow = piv + (size_t)(y0 + row) * nx * es;
+#pragma unroll
+          for (int m = 0; m < V; ++m) sv[m] = load2<ST>(prow, 2 * (size_t)(t + T * m));
+          if (!cta_wait(bar, phase, p.status, flag, expire)) {
+            alive = false;
+            break;
+          }
+          expire = false;
+          phase ^= 1;
+          const unsigned char* st_row = stage + (size_t)g * nx * es;
+#pragma unroll
+          for (int m = 0; m < V; ++m) {
+            const float2 a = load2<ST>(st_row, 2 * (size_t)(t + T * m));
+            v[m] = make_float2(a.x - sv[m].x, a.y - sv[m].y);
+          }
+          __syncthreads();   // stage consumed
+          if (threadIdx.x == 0) {
+            const int s = (k - 1) * rounds + r + 1;
+            if (s < steps) issue(q, s);
+            else if (q + gridDim.x < Q) issue(q + gridDim.x, 0);
+          }
+          float acc[2 * V];
+          if (k == 1) {
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+              acc[2 * m] = v[m].x;
+              acc[2 * m + 1] = v[m].y;
+            }
+          } else {
+            sum_load(r, acc);   // the sums stored for the previous member
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+              acc[2 * m] += v[m].x;
+              acc[2 * m + 1] += v[m].y;
+            }
+          }
+          sum_store(r, acc);
+        } else {
+          float acc[2 * V];
+          sum_load(r, acc);
+#pragma unroll
+          for (int m = 0; m < V; ++m) v[m] = make_float2(acc[2 * m] * p.inv_sqrt_N, acc[2 * m + 1] * p.inv_sqrt_N);
+        }
+        float2* line = lines + row * pitch;
+        fft_line<L, V, false>(v, line, t, p.twL, line_bar<T>(g));
+#pragma unroll
+        for (int m = 0; m < V; ++m) line[pidx(t + T * m)] = v[m];
+      }
+      if (!alive) break;
+      __syncthreads();
+      const size_t f = (size_t)jb * N + (k < N ? k : 0);
+      row_twist_store<L>(lines, p.out + f * (size_t)L * p.ny, p.R, p.ny, y0, p.twX);
+      __syncthreads();
+    }
+  }
+  if (in_tm) {
+    tm_wait_st();
+    tm_fence_before_sync();
+  }
+  __syncthreads();
+  if (in_tm && (threadIdx.x >> 5) == 0) tm_dealloc(*tslot, (uint32_t)p.tm_alloc);
 }
 
 // Inverse row pass.  A work item is R rows of one field (R = the rows the CTA
@@ -307,6 +473,44 @@ inline RowShape row_shape(int L, int V, int ny, int nx, int es, int n_in, bool h
   }
 }
 
+// Anomaly rows: the row shape of row_shape, with R halved (down to one round) until the running
+// sums fit the tensor memory: rounds x 2V columns per thread, threads 128 apart sharing a lane.
+template <int L, int V, int ST>
+cudaError_t row_anom_LV(RowFwdParams p, cudaStream_t st) {
+  constexpr int es = ST == kBF16 ? 2 : 4;
+  RowShape s = row_shape(L, V, p.ny, p.nx, es, 1, (p.vsel & 2) != 0);
+  const int threads = s.T * s.LPC;
+  const int share = (threads + 127) / 128;
+  const bool in_tm = threads % 32 == 0;   // tensor-memory loads and stores take whole warps
+  int alloc = 0;
+  for (;;) {
+    p.tm_cols = (s.R / s.LPC) * 2 * V;
+    alloc = 32;
+    while (alloc < share * p.tm_cols) alloc <<= 1;
+    if (!in_tm || alloc <= 512 || s.R <= s.LPC) break;
+    s.R >>= 1;
+  }
+  s.smem = (((size_t)s.R * row_pitch(L) * sizeof(float2) + 127) & ~(size_t)127) + (size_t)s.LPC * p.nx * es + 16;
+  if (!in_tm) s.smem += (size_t)threads * p.tm_cols * sizeof(float);
+  if ((in_tm && alloc > 512) || s.smem > 227 * 1024 || s.R < 2) return cudaErrorInvalidConfiguration;
+  p.tm_alloc = in_tm ? alloc : 0;
+  p.R = s.R;
+  p.n_tiles = p.ny / s.R;
+  p.inv_sqrt_N = (float)(1.0 / std::sqrt((double)p.N));
+  auto kern = row_anom_kernel<L, V, ST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, s.smem);
+  if (in_tm && per_sm > 512 / alloc) per_sm = 512 / alloc;   // co-resident CTAs never wait for tensor memory
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)p.M * p.n_tiles;
+  const long long cap = (long long)sm_count() * per_sm;
+  if (grid > cap) grid = cap;
+  kern<<<(unsigned)grid, threads, s.smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 template <int L, int V, int ST, int MODE>
 cudaError_t row_fwd_LV(RowFwdParams p, int n_fields, cudaStream_t st) {
   constexpr int es = ST == kBF16 ? 2 : 4;
@@ -372,8 +576,8 @@ cudaError_t row_inv_LV(RowInvParams p, int n_fields, cudaStream_t st) {
 template <int L, int ST>
 cudaError_t row_fwd_L(const RowFwdParams& p, int n_fields, cudaStream_t st) {
   if (p.mode == kAnomaly) {
-    if (p.vsel & 1) return row_fwd_LV<L, plan_V(L, 1), ST, kAnomaly>(p, n_fields, st);
-    return row_fwd_LV<L, plan_V(L, 0), ST, kAnomaly>(p, n_fields, st);
+    if (p.vsel & 1) return row_anom_LV<L, plan_V(L, 1), ST>(p, st);
+    return row_anom_LV<L, plan_V(L, 0), ST>(p, st);
   }
   if (p.mode == kInnovationDrawn) {
     if (p.vsel & 1) return row_fwd_LV<L, plan_V(L, 1), ST, kInnovationDrawn>(p, n_fields, st);

@@ -1,6 +1,6 @@
 // Spectral covariance estimate without any device allocation: the same passes
 // as fftenkf_estimate_spectrum for one block, with every scratch buffer
-// (twiddle tables, status word, member mean, row spectra, covariance table)
+// (twiddle tables, status word, row spectra, covariance table)
 // carved out of one file-scope __device__ array instead of a workspace.
 //
 // The array lives in the library's device image, so every GPU that loads the
@@ -115,13 +115,12 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble,
   if (col_stats_smem(ny, 1, 0, nullptr) == 0) return sfail(FFTENKF_EUNSUPPORTED, "column statistics do not fit in shared memory");
   const int L = nx / 2;
   const int Vl = plan_V(L, 0), Vy = plan_V(ny, 0);
-  const size_t G = (size_t)ny * nx, K1 = (size_t)ny * (L + 1);
+  const size_t K1 = (size_t)ny * (L + 1);
   size_t off = 0;
   const size_t off_status = off;  off = rup(off + sizeof(int));
   const size_t off_twL = off;     off = rup(off + (size_t)twiddle_count(L, Vl) * sizeof(float2));
   const size_t off_twY = off;     off = rup(off + (size_t)twiddle_count(ny, Vy) * sizeof(float2));
   const size_t off_twX = off;     off = rup(off + (size_t)(L + 1) * sizeof(float2));
-  const size_t off_mean = off;    off = rup(off + G * sizeof(float));
   const size_t off_A = off;       off = rup(off + (size_t)n_members * L * ny * sizeof(float2));
   const size_t off_chat = off;    off = rup(off + K1 * sizeof(float));
   if (off > kStaticScratchBytes)
@@ -142,20 +141,10 @@ extern "C" fftenkf_status fftenkf_estimate_spectrum_static(const void* ensemble,
     plain_twiddles_kernel<<<16, 256, 0, s>>>(twX, nx, L + 1);
     e = cudaGetLastError();
   }
-  MeanParams mp;
-  mp.M = 1;
-  mp.N = n_members;
-  mp.storage = storage;
-  mp.G = (long long)G;
-  mp.ens = ensemble;
-  mp.mean = reinterpret_cast<float*>(base + off_mean);
-  mp.status = status;
-  mp.vsel = 0;
-  if (e == cudaSuccess) e = launch_mean(mp, s);
   RowFwdParams rp;
   memset(&rp, 0, sizeof(rp));
   rp.ny = ny; rp.nx = nx; rp.L = L; rp.M = 1; rp.N = n_members; rp.n_obs = 1; rp.mode = kAnomaly;
-  rp.storage = storage; rp.ens = ensemble; rp.mean = mp.mean;
+  rp.storage = storage; rp.ens = ensemble;
   rp.out = reinterpret_cast<float2*>(base + off_A);
   rp.twL = twL; rp.twX = twX; rp.status = status; rp.vsel = 0;
   if (e == cudaSuccess) e = launch_row_fwd(rp, n_members, s);
