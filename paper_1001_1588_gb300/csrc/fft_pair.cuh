@@ -250,6 +250,53 @@ struct PStage {
   }
 };
 
+// As PStage, with the exchanges alternating between two buffers (even exchanges in sa, odd
+// ones in sb), so that no barrier separates one exchange's reads from the next one's writes:
+// a thread writes sb only after the barrier of the previous exchange, which every thread
+// reaches after its last read of sb, and likewise for sa.  With an odd number of exchanges the
+// last one is followed by a barrier, so that the next transform may start again in sa.
+template <int N, int V, int S, int NS, bool INV>
+struct PStage2 {
+  static __device__ __forceinline__ void run(cp (&v)[V], float4* sa, float4* sb, int t, const float4* __restrict__ tw,
+                                             int bid) {
+    constexpr int R = radix_at(N, V, S);
+    constexpr int T = N / V;
+    constexpr int B = V / R;
+    constexpr int SH = pair_pad_shift(N, V);
+    constexpr bool LAST = (S == num_stages(N, V) - 1);
+    float4* sm = (S % 2 == 0) ? sa : sb;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      cp a[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[r] = v[b + r * B];
+      const int j = t + T * b;
+      if (NS > 1) {
+        float2 wr[R], wi[R];
+        pair_twiddle_powers<R, INV>(wr, wi, tw + twiddle_offset(N, V, S) + (j % NS), NS);
+#pragma unroll
+        for (int r = 1; r < R; ++r) a[r] = cp_mulw(a[r], wr[r], wi[r]);
+      }
+      PDft<R, INV>::run(a);
+      if (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b + r * B] = a[r];
+      } else {
+        const int p = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[ppidx<SH>(p + r * NS)] = cp_pack(a[r]);
+      }
+    }
+    if constexpr (!LAST) {
+      line_sync<T>(bid);
+#pragma unroll
+      for (int m = 0; m < V; ++m) v[m] = cp_unpack(sm[ppidx<SH>(t + T * m)]);
+      if constexpr (S + 2 == num_stages(N, V) && (num_stages(N, V) - 1) % 2 == 1) line_sync<T>(bid);
+      PStage2<N, V, S + 1, NS * R, INV>::run(v, sa, sb, t, tw, bid);
+    }
+  }
+};
+
 // Unnormalised DFT of two lines at once, sign -1 (forward) or +1 (INV); the
 // calling conventions (bid, TRAIL, canonical distribution) are those of
 // fft_line.  sm: the pair's buffer of pair_padded_len(N, V) 16-byte slots.
@@ -258,6 +305,18 @@ __device__ __forceinline__ void fft_pair(cp (&v)[V], float4* sm, int t, const fl
   static_assert(N % V == 0, "V must divide N");
   static_assert(num_stages(N, V) > 0, "no radix plan");
   PStage<N, V, 0, 1, INV, TRAIL>::run(v, sm, t, tw, bid);
+}
+
+// Two-buffer form (PStage2): each exchange takes one barrier.  Every thread of the line (bid)
+// calls it; sa and sb hold pair_padded_len(N, V) slots each; on return both may be written
+// again by the next transform's exchanges (which start in sa), but not by anything else
+// before a barrier of the line.
+template <int N, int V, bool INV>
+__device__ __forceinline__ void fft_pair2(cp (&v)[V], float4* sa, float4* sb, int t, const float4* __restrict__ tw,
+                                          int bid = 0) {
+  static_assert(N % V == 0, "V must divide N");
+  static_assert(num_stages(N, V) > 0, "no radix plan");
+  PStage2<N, V, 0, 1, INV>::run(v, sa, sb, t, tw, bid);
 }
 
 }  // namespace fftenkf

@@ -19,9 +19,12 @@
 // a time, and each pair of lines is transformed at once in paired FP32
 // (fft_pair.cuh); the observed pair (or the observed block and its partner) is
 // transformed first, so the cross terms of every later pair find it in
-// registers.  Lines arrive by bulk copies into two stages, one unit (two lines)
-// ahead; every group has its own stages, barriers and column sequence, so the
-// groups of a CTA never wait for one another.
+// tensor memory.  Lines arrive by bulk copies into two stage slots, one unit (two
+// lines) ahead; once a unit's lines are read, its slot is the second exchange
+// buffer of that unit's transforms, which alternate between it and the group's
+// exchange buffer and so take one barrier per exchange.  Every group has its own
+// slots, barriers and column sequence, so the groups of a CTA never wait for one
+// another.
 #pragma once
 #include "common.cuh"
 #include "fft_pair.cuh"
@@ -36,7 +39,10 @@ struct ColFusedShape {
   static constexpr int T = NY / V;
   static constexpr int PL = (pair_padded_len(NY, V) + 7) & ~7;           // 16-byte exchange slots
   static constexpr size_t stage_bytes = (size_t)2 * NY * sizeof(float2);   // one unit: two lines
-  static constexpr size_t group_bytes = ((2 * stage_bytes + (size_t)PL * 16 + 32) + 127) & ~(size_t)127;
+  // a stage slot also serves as the second exchange buffer once its unit is read
+  static constexpr size_t slot_bytes =
+      ((stage_bytes > (size_t)PL * 16 ? stage_bytes : (size_t)PL * 16) + 127) & ~(size_t)127;
+  static constexpr size_t group_bytes = ((2 * slot_bytes + (size_t)PL * 16 + 32) + 127) & ~(size_t)127;
 };
 
 // tensor-memory columns of one thread when a CTA of `threads` threads shares the 128 lanes x
@@ -317,9 +323,10 @@ __global__ void __launch_bounds__(V <= 8 ? 512 : 256, 1) col_fused_kernel(const 
   const int t = threadIdx.x - g * T;
   const int bid = (T == 32) ? -1 : 1 + g;
   unsigned char* gb = smraw + (size_t)g * Sh::group_bytes;
-  float2* stage = reinterpret_cast<float2*>(gb);   // [2 stages][2 lines][NY]
-  float4* xbuf = reinterpret_cast<float4*>(gb + 2 * Sh::stage_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gb + 2 * Sh::stage_bytes + (size_t)Sh::PL * 16);
+  // [2 stage slots][2 lines][NY] (slots of slot_bytes)
+  auto slot = [&](int b) { return gb + (size_t)b * Sh::slot_bytes; };
+  float4* xbuf = reinterpret_cast<float4*>(gb + 2 * Sh::slot_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gb + 2 * Sh::slot_bytes + (size_t)Sh::PL * 16);
   int* gflag = reinterpret_cast<int*>(bars + 2);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smraw + (size_t)LPC * Sh::group_bytes);
 
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(V <= 8 ? 512 : 256, 1) col_fused_kernel(const 
       src0 = p.W + ((size_t)k * p.n_obs) * fstride + (size_t)col * NY;
       if (p.n_obs == 2) src1 = p.W + ((size_t)k * p.n_obs + 1) * fstride + (size_t)col * NY;
     }
-    float2* dst = stage + (size_t)b * 2 * NY;
+    float2* dst = reinterpret_cast<float2*>(slot(b));
     mbar_arrive_expect_tx(&bars[b], (uint32_t)((src1 ? 2 : 1) * NY * sizeof(float2)));
     bulk_g2s(dst, src0, NY * sizeof(float2), &bars[b]);
     if (src1) bulk_g2s(dst + NY, src1, NY * sizeof(float2), &bars[b]);
@@ -406,31 +413,34 @@ __global__ void __launch_bounds__(V <= 8 ? 512 : 256, 1) col_fused_kernel(const 
         break;
       }
       if (b) ph1 ^= 1; else ph0 ^= 1;
+      // every thread of the group has left the previous unit (its reads of the other slot,
+      // as a stage and as an exchange buffer): that slot takes the next unit's copy
+      if (t == 0 && consumed > 0) issue_next();
       const bool stats = u < units_stats;
       const int pp = stats ? u % P : 0;
       const bool has1 = stats ? (2 * pp + 1 < M) : (p.n_obs == 2);
       cp v[V];
-      const float2* l0 = stage + (size_t)b * 2 * NY;
+      const float2* l0 = reinterpret_cast<const float2*>(slot(b));
       read_pair<NY, V>(v, l0, l0 + NY, has1, t, part);
-      line_sync<T>(bid);   // stage consumed
       ++consumed;
-      if (t == 0) issue_next();
+      // the unit's slot, read, is the second exchange buffer: its first write follows the first
+      // exchange's barrier, which every thread reaches after read_pair
+      float4* xb2 = reinterpret_cast<float4*>(slot(b));
       if (stats) {
-        // the exchange buffer is next written after the next unit's barriers
-        fft_pair<NY, V, false, false>(v, xbuf, t, p.tw, bid);
+        fft_pair2<NY, V, false>(v, xbuf, xb2, t, p.tw, bid);
         if (pp == 0) store_halves<V>(v, ta + KB);
         fused_accumulate<V, NOBS>(v, pp, M, p.n_obs, ta, KB, u < P ? -1.f : 1.f);   // units of member 0 first
         if (u == units_stats - 1) bad |= !fused_gains<NY, V, NOBS>(p, ta, c, t);
       } else {
         const int k = u - units_stats;
-        fft_pair<NY, V, false, true>(v, xbuf, t, p.tw, bid);   // what; the buffer is reused at once
+        fft_pair2<NY, V, false>(v, xbuf, xb2, t, p.tw, bid);   // what
         if constexpr (DRAWN) fused_add_drawn<NY, V, NOBS>(v, p, k, c, t);
         store_halves<V>(v, ta + KB);
 #pragma unroll 1
         for (int tp = 0; tp < P; ++tp) {
           cp s[V];
           fused_targets<V, NOBS>(s, tp, M, p.n_obs, ta, KB);
-          fft_pair<NY, V, true, true>(s, xbuf, t, p.tw, bid);
+          fft_pair2<NY, V, true>(s, xbuf, xb2, t, p.tw, bid);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = 2 * tp + h;
@@ -478,7 +488,9 @@ inline ColFusedLaunch col_fused_launch(int ny, int sel) {
   const int max_threads = s.V <= 8 ? 512 : 256;
   if (s.T < 32 || s.T % 32 || s.T > max_threads) return s;
   const size_t pl = (size_t)((pair_padded_len(ny, s.V) + 7) & ~7);
-  const size_t group = ((2 * (size_t)2 * ny * sizeof(float2) + pl * 16 + 32) + 127) & ~(size_t)127;
+  const size_t stage = (size_t)2 * ny * sizeof(float2);
+  const size_t slot = ((stage > pl * 16 ? stage : pl * 16) + 127) & ~(size_t)127;   // as ColFusedShape
+  const size_t group = ((2 * slot + pl * 16 + 32) + 127) & ~(size_t)127;
   int lpc = max_threads / s.T;
   while (lpc > 0 && (size_t)lpc * group + 16 > (size_t)227 * 1024) --lpc;
   s.lpc = lpc;
