@@ -88,6 +88,13 @@ fftenkf_status fftenkf_spectrum_size(fftenkf_plan plan, size_t* n_doubles);
 /* Steps 1-2 of Sec. 2.1 (eq. dii, eq. cov-multi-spectral): the spectral
  * covariance tables of `ensemble` ([M][N][ny][nx], storage dtype), unitary
  * scaling, written to spectrum_out (device, fftenkf_spectrum_size doubles).
+ * No mean field is formed: the first member of every block is the pivot, the
+ * differences u_k - u_0 are transformed (exact in FP32 for BF16 members, and for
+ * FP32 members within a factor two of each other), and the products of the
+ * transformed sum of those differences are subtracted from the accumulated ones,
+ * which gives the same sample covariance.  Where the ensemble has no variance
+ * above FFT round-off an auto table entry can then come out a few rounding
+ * errors below 0.
  * workspace: device buffer of fftenkf_workspace_size bytes, or NULL to use a
  * buffer the plan allocates on first use and keeps. */
 fftenkf_status fftenkf_estimate_spectrum(fftenkf_plan plan, const void* ensemble, double* spectrum_out,
@@ -179,7 +186,9 @@ fftenkf_status fftenkf_set_expire_first_wait(fftenkf_plan plan, int on);
  * fftenkf_pass_times waits for those events, writes for every pass p <
  * n_passes its total device milliseconds and number of launches since the
  * last read (or enable), and resets the totals.  Passes are numbered
- * 0..fftenkf_pass_count()-1 and named by fftenkf_pass_name. */
+ * 0..fftenkf_pass_count()-1 and named by fftenkf_pass_name.  Pass 0 ("mean")
+ * is retired (the anomaly rows take the first member as pivot): it keeps its
+ * number so that the others keep theirs, and always reports 0 launches. */
 fftenkf_status fftenkf_set_profiling(fftenkf_plan plan, int enable);
 fftenkf_status fftenkf_pass_times(fftenkf_plan plan, double* total_ms, int* launches, int n_passes);
 int fftenkf_pass_count(void);
