@@ -56,12 +56,13 @@ def parse():
                     help="sine workload: skip the side timing of the periodic extension-size analysis")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP32-storage run of the headline draw (the equal-RMSE precision comparison)")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "coupled", "sine", "morph", "compare"],
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "coupled", "sine", "morph", "compare", "oracle"],
                     help="large: 4 blocks 4096^2 N=20 (default, the headline); batched: 256 mixed analyses; "
                          "coupled: 3 blocks 4096^2 N=20 with coupled observed blocks; "
                          "sine: real sine transform variant on 2049^2 nodes, 4 blocks, N=20; "
                          "compare: precision, learned-spectrum and batched forms at equal analysis RMSE; "
-                         "morph: morphing FFT EnKF, 2 blocks 4096^2 N=20 FP32 (T_x, T_y, r^(1) observed)")
+                         "morph: morphing FFT EnKF, 2 blocks 4096^2 N=20 FP32 (T_x, T_y, r^(1) observed); "
+                         "oracle: the FP64 oracle's host times on configs 1, 2, the 1024^2 shape and a batched sample")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fused-schedule", default="auto", choices=["auto", "0", "1"],
@@ -311,6 +312,52 @@ def cpu_threads():
         return max(int(i.get("num_threads", 1)) for i in threadpool_info()) or os.cpu_count()
     except Exception:
         return os.cpu_count()
+
+
+def run_oracle_configs(a):
+    """Host timings of the FP64 oracle (oracle.enkf.analyze: estimate, gains and update with the
+    explicit DFT) on the parity configurations: 1 and 2 in full, the learned-spectrum shape (1024^2,
+    N=5, one block) in full, and a sample of the batched workload (the cheapest item of every side
+    length).  A baseline only; one JSON line, no GPU."""
+    import numpy as np
+    from oracle import enkf
+    from synth import fields
+    threads = cpu_threads()
+
+    def timed(p):
+        t0 = time.perf_counter()
+        enkf.analyze(p.ensemble, p.data, p.perturbations, p.rhat, p.observed)
+        return time.perf_counter() - t0
+
+    res = {}
+    for name, p in (("1: 1 block 64^2, N=5", fields.make_config1()),
+                    ("2: 3 blocks 512^2, N=5", fields.make_config2())):
+        t = timed(p)
+        res[name] = {"seconds": t, "value": p.ny * p.nx * p.N / t}
+    S = fields.powerlaw_spectrum(1024, 1024, 8.0, -3.5)
+    p5 = fields.make_problem(1024, 1024, 5, [S], [1], np.full((1, 1024, 513), 0.1), 20260005, "f32")
+    t = timed(p5)
+    res["5: 1 block 1024^2, N=5 (plain estimate)"] = {"seconds": t, "value": p5.ny * p5.nx * p5.N / t}
+    best = {}
+    for it in fields.batched_item_params():
+        side = max(it["ny"], it["nx"])
+        cost = it["ny"] * it["nx"] * it["N"]
+        if side not in best or cost < best[side]["ny"] * best[side]["nx"] * best[side]["N"]:
+            best[side] = it
+    tot_t, tot_u = 0.0, 0.0
+    for it in best.values():
+        S = fields.se_spectrum(it["ny"], it["nx"], it["ell"], 1.0)
+        p = fields.make_problem(it["ny"], it["nx"], it["N"], [S], [1],
+                                np.full((1, it["ny"], it["nx"] // 2 + 1), it["r"]), it["seed"], "f32")
+        tot_t += timed(p)
+        tot_u += it["ny"] * it["nx"] * it["N"]
+    res["4: sample of %d batched items (the cheapest of every side)" % len(best)] = {
+        "seconds": tot_t, "value": tot_u / tot_t}
+    print(json.dumps({"metric": "FP64 oracle analysis, grid-pts*members/s on the host cores", "unit": UNIT,
+                      "workload": "oracle", "kind": "oracle", "cores": threads, "configs": res,
+                      "note": "oracle.enkf.analyze (explicit unitary DFT by dense DFT-matrix products, FP64); "
+                              "a baseline, not a target"}))
+    return 0
 
 
 def run_reference(a):
@@ -1090,6 +1137,8 @@ def main():
         return run_sine(a)
     if a.workload == "morph":
         return run_morph(a)
+    if a.workload == "oracle":
+        return run_oracle_configs(a)
     if a.workload == "compare":
         return run_compare(a)
     return run_ours(a)

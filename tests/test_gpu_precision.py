@@ -1,9 +1,10 @@
 """GPU parity where the precision rules of the analysis matter, and the bounded-wait error path.
 
 * A large common mean (300 with unit anomalies), FP32 and BF16 storage: the ensemble mean of
-  eq. (dii) is subtracted from values 300 times the anomalies; the member mean is an error-free
-  FP32 sum divided with a remainder correction, the innovation d + e - u is formed as
-  (d - u) + e (d - u exact for close values).  Gates: the analysis and the spectrum tables at the
+  eq. (dii) would be subtracted from values 300 times the anomalies; the library never forms it,
+  but transforms the differences from the first member (exact for close values) and subtracts
+  the products of their transformed sum, and forms the innovation d + e - u as (d - u) + e
+  (d - u exact for close values).  Gates: the analysis and the spectrum tables at the
   storage tolerance (1e-5 FP32, 5e-3 BF16, relative L2 over the whole array); for FP32 the
   increment u^a - u at 1e-4 (the forecast, 300 times larger, would hide an increment error in the
   analysis).  With BF16 storage the output itself is rounded at 300 (spacing 2), so only the
