@@ -473,7 +473,7 @@ def compare_batched(dev, count=256, steps=5):
     return out
 
 
-def compare_learned(dev, grid=1024, pairs=4096, epochs=12, n_draws=32, steps=5):
+def compare_learned(dev, grid=1024, pairs=20000, epochs=12, n_draws=64, steps=5):
     """Learned against plain spectrum at grid^2, N = 5 (the learned-spectrum config): the MLP is
     trained on the GPU by the library's kernels on `pairs` (N = 5 estimate, N = 500 target) pairs,
     then analysis RMSE over held-out draws for the plain estimate, the learned spectrum and the true

@@ -116,6 +116,18 @@ __device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M
                                                  float sg) {
   const int XB = n_obs * V;
   tm_wait_st();   // the sums (and the member's spectra) stored by earlier units
+  if (2 * pp + 1 < n_obs) {   // both roles observed: their auto sums are adjacent, one load
+    float a[2 * V];
+    tm_ld<2 * V>(ta + 2 * pp * V, a);
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+      const float2 x0 = half_of<0>(v[m]), x1 = half_of<1>(v[m]);
+      a[m] = fmaf(sg * x0.x, x0.x, fmaf(sg * x0.y, x0.y, a[m]));
+      a[V + m] = fmaf(sg * x1.x, x1.x, fmaf(sg * x1.y, x1.y, a[V + m]));
+    }
+    tm_st<2 * V>(ta + 2 * pp * V, a);
+    return;
+  }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int r = 2 * pp + h;
@@ -136,8 +148,7 @@ __device__ __forceinline__ void fused_accumulate(const cp (&v)[V], int pp, int M
         if (i >= n_obs) continue;
         const uint32_t at = ta + XB + (u * n_obs + i) * 2 * V;
         float a[2 * V], o[2 * V];
-        tm_ld<2 * V>(at, a);
-        tm_ld<2 * V>(ta + KB + 2 * V * i, o);
+        tm_ld2<2 * V, 2 * V>(at, a, ta + KB + 2 * V * i, o);
 #pragma unroll
         for (int m = 0; m < V; ++m) {   // += sg x conj(o)
           float2 x = h ? half_of<1>(v[m]) : half_of<0>(v[m]);
@@ -243,8 +254,7 @@ __device__ __forceinline__ void fused_targets(cp (&s)[V], int tp, int M, int n_o
     if (r >= M) continue;
     if (r < n_obs) {   // an observed block: its own innovation times G^(oo)
       float gv[V], x[2 * V];
-      tm_ld<V>(ta + r * V, gv);
-      tm_ld<2 * V>(ta + KB + 2 * V * r, x);
+      tm_ld2<V, 2 * V>(ta + r * V, gv, ta + KB + 2 * V * r, x);
 #pragma unroll
       for (int m = 0; m < V; ++m) {
         const float2 y = make_float2(gv[m] * x[2 * m], gv[m] * x[2 * m + 1]);
@@ -256,8 +266,7 @@ __device__ __forceinline__ void fused_targets(cp (&s)[V], int tp, int M, int n_o
       for (int i = 0; i < NOBS; ++i) {
         if (i >= n_obs) continue;
         float gx[2 * V], x[2 * V];
-        tm_ld<2 * V>(ta + XB + (u * n_obs + i) * 2 * V, gx);
-        tm_ld<2 * V>(ta + KB + 2 * V * i, x);
+        tm_ld2<2 * V, 2 * V>(ta + XB + (u * n_obs + i) * 2 * V, gx, ta + KB + 2 * V * i, x);
 #pragma unroll
         for (int m = 0; m < V; ++m) {
           float2 acc = h ? half_of<1>(s[m]) : half_of<0>(s[m]);

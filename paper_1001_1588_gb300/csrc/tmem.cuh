@@ -11,8 +11,9 @@
 // exchanges.
 //
 // Every load here waits for its data in the same asm statement, so no register is
-// read early.  Stores are asynchronous: a caller that reads columns it stored
-// earlier calls tm_wait_st() first (once, before a batch of loads).
+// read early (tm_ld2: two loads, then one wait, in one statement).  Stores
+// are asynchronous: a caller that reads columns it stored earlier calls
+// tm_wait_st() first (once, before a batch of loads).
 #pragma once
 #include <stdint.h>
 
@@ -129,6 +130,54 @@ __device__ __forceinline__ void tm_st(uint32_t a, const float* r) {
       tm_st8(a + c, r + c);
       c += 8;
     }
+  }
+}
+
+// two loads and one wait in one asm statement: 16 + 32 or 32 + 32 columns
+__device__ __forceinline__ void tm_ld16_32(uint32_t a1, float* r, uint32_t a2, float* q) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%49];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+        "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]),
+        "=f"(q[0]), "=f"(q[1]), "=f"(q[2]), "=f"(q[3]), "=f"(q[4]), "=f"(q[5]), "=f"(q[6]), "=f"(q[7]), "=f"(q[8]),
+        "=f"(q[9]), "=f"(q[10]), "=f"(q[11]), "=f"(q[12]), "=f"(q[13]), "=f"(q[14]), "=f"(q[15]), "=f"(q[16]),
+        "=f"(q[17]), "=f"(q[18]), "=f"(q[19]), "=f"(q[20]), "=f"(q[21]), "=f"(q[22]), "=f"(q[23]), "=f"(q[24]),
+        "=f"(q[25]), "=f"(q[26]), "=f"(q[27]), "=f"(q[28]), "=f"(q[29]), "=f"(q[30]), "=f"(q[31])
+      : "r"(a1), "r"(a2)
+      : "memory");
+}
+__device__ __forceinline__ void tm_ld32_32(uint32_t a1, float* r, uint32_t a2, float* q) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+        "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]), "=f"(r[16]),
+        "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]),
+        "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]),
+        "=f"(q[0]), "=f"(q[1]), "=f"(q[2]), "=f"(q[3]), "=f"(q[4]), "=f"(q[5]), "=f"(q[6]), "=f"(q[7]), "=f"(q[8]),
+        "=f"(q[9]), "=f"(q[10]), "=f"(q[11]), "=f"(q[12]), "=f"(q[13]), "=f"(q[14]), "=f"(q[15]), "=f"(q[16]),
+        "=f"(q[17]), "=f"(q[18]), "=f"(q[19]), "=f"(q[20]), "=f"(q[21]), "=f"(q[22]), "=f"(q[23]), "=f"(q[24]),
+        "=f"(q[25]), "=f"(q[26]), "=f"(q[27]), "=f"(q[28]), "=f"(q[29]), "=f"(q[30]), "=f"(q[31])
+      : "r"(a1), "r"(a2)
+      : "memory");
+}
+// n1 columns at a1 and n2 at a2, one wait for both where a single statement covers the pair
+// (16 + 32, 32 + 32); otherwise two waited loads
+template <int n1, int n2>
+__device__ __forceinline__ void tm_ld2(uint32_t a1, float* r1, uint32_t a2, float* r2) {
+  if constexpr (n1 == 16 && n2 == 32) {
+    tm_ld16_32(a1, r1, a2, r2);
+  } else if constexpr (n1 == 32 && n2 == 32) {
+    tm_ld32_32(a1, r1, a2, r2);
+  } else {
+    tm_ld<n1>(a1, r1);
+    tm_ld<n2>(a2, r2);
   }
 }
 
