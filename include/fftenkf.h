@@ -229,10 +229,14 @@ fftenkf_status fftenkf_set_coupled(fftenkf_plan plan, int coupled);
 
 /* ---------------------------------------------------------------- batched
  * Many independent analyses of uneven sizes (the block-state method with one
- * fully observed block each, H = I, eq. spectral-enkf): every pass is one
- * persistent launch over a work list mixing the units of all analyses, and
- * the seven launches are replayed as one CUDA graph (captured on the first
- * call and after every autotune).  dims[i].n_blocks must be 1; all analyses
+ * fully observed block each, H = I, eq. spectral-enkf), replayed as one CUDA
+ * graph (captured on the first call, after every autotune, and when the
+ * pointers of an analysis of at least 512 x 256 points change).  Analyses of at
+ * least 512 x 256 grid points run through the single-analysis passes (one plan
+ * each, created with the batch), issued on eight graph branches, largest first,
+ * each to the branch with the least work; every other analysis goes through
+ * seven persistent launches, each over a work list mixing the units of all of
+ * them, on a branch of its own.  dims[i].n_blocks must be 1; all analyses
  * share one storage type; ny and nx/2 in {2^a, 3*2^a} between 16 and 1024.
  * The pointer arguments of fftenkf_analyze_batched are HOST arrays of `count`
  * DEVICE pointers with the single-analysis layouts (ensemble [N][ny][nx],

@@ -1,7 +1,14 @@
 // C ABI of the batched analyses: plan (work lists, workspace layout, twiddle
 // tables), autotuner (CTA size and line-FFT schedule per pass, chosen by
 // timing the candidates on scratch data of the batch's shapes), and the
-// analysis itself, replayed as one CUDA graph of seven persistent launches.
+// analysis itself, replayed as one CUDA graph.
+//
+// Analyses of at least kBigPoints grid points run through the single-analysis
+// passes (one plan each, whose pipelined row and column kernels move their
+// bytes at several times the rate of the persistent batched passes); they are
+// issued on kLanes streams that branch off the capture (largest first, each to
+// the lane with the least work so far), beside the seven persistent launches
+// that take every smaller analysis, so that the branches fill the GPU together.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,6 +34,14 @@ fftenkf_status bfail(fftenkf_status s, const std::string& m) {
 }
 size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 const int kCandBt[2] = {128, 256};
+#ifndef FFTENKF_BATCH_BIG_POINTS
+#define FFTENKF_BATCH_BIG_POINTS (512LL * 256)
+#endif
+#ifndef FFTENKF_BATCH_LANES
+#define FFTENKF_BATCH_LANES 8
+#endif
+constexpr long long kBigPoints = FFTENKF_BATCH_BIG_POINTS;   // grid points from which an analysis takes its own plan
+constexpr int kLanes = FFTENKF_BATCH_LANES;
 }  // namespace
 
 struct fftenkf_batch_s {
@@ -44,11 +59,17 @@ struct fftenkf_batch_s {
   int n_units[kBPassCount] = {};
   size_t smem[kBPassCount] = {};
   int grid[kBPassCount] = {};
-  // graph of the seven launches
+  // analyses on their own plans (null: in the batched passes), their workspace regions
+  std::vector<fftenkf_plan> sub;
+  std::vector<size_t> off_sub;
+  cudaStream_t lane[kLanes] = {};
+  cudaEvent_t ev_fork = nullptr, ev_lane[kLanes] = {};
+  // graph of the launches
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   char* bound_ws = nullptr;
   bool items_dirty = true;
+  bool sub_dirty = true;   // pointers of a planned analysis changed: capture again
 };
 
 // work list and launch shape of pass `pass` for CTA size bt and schedule vsel
@@ -60,6 +81,7 @@ static fftenkf_status build_pass(fftenkf_batch b, int pass, int bt, int vsel) {
   std::vector<U> list;
   size_t smem = 0;
   for (int i = 0; i < b->count; ++i) {
+    if (b->sub[i]) continue;   // on its own plan
     const BatchItem& it = b->items[i];
     const int n = batch_units(pass, it, bt, vsel);
     const double c = batch_unit_cost(pass, it, bt, vsel);
@@ -106,10 +128,50 @@ static BatchParams pass_params(fftenkf_batch b, int pass) {
 
 static cudaError_t run_passes(fftenkf_batch b, cudaStream_t s) {
   for (int pass = 0; pass < kBPassCount; ++pass) {
+    if (b->n_units[pass] == 0) continue;   // every analysis on its own plan
     cudaError_t e = launch_batch_pass(pass, pass_params(b, pass), b->bt[pass], b->smem[pass], b->grid[pass], s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// The whole batch on stream s: the planned analyses on the lanes (forked from s and joined
+// back), the persistent passes of the others on s.
+static fftenkf_status run_all(fftenkf_batch b, void* const* ens, const float* const* data, const void* const* pert,
+                              const double* const* rhat, char* ws, cudaStream_t s) {
+  bool any = false;
+  for (int i = 0; i < b->count; ++i) any |= b->sub[i] != nullptr;
+  cudaError_t e = cudaSuccess;
+  if (any) {
+    e = cudaEventRecord(b->ev_fork, s);
+    for (int l = 0; l < kLanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->lane[l], b->ev_fork, 0);
+    if (e != cudaSuccess) return bfail(FFTENKF_ECUDA, std::string("fork: ") + cudaGetErrorString(e));
+    std::vector<int> order;
+    for (int i = 0; i < b->count; ++i)
+      if (b->sub[i]) order.push_back(i);
+    auto cost = [&](int i) { return (double)b->items[i].N * b->items[i].ny * b->items[i].nx; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    double load[kLanes] = {};
+    for (int i : order) {
+      int l = 0;
+      for (int q = 1; q < kLanes; ++q)
+        if (load[q] < load[l]) l = q;
+      load[l] += cost(i);
+      fftenkf_status st = fftenkf_analyze(b->sub[i], ens[i], data[i], pert[i], rhat[i], nullptr, ws + b->off_sub[i],
+                                          b->lane[l]);
+      if (st != FFTENKF_OK) return st;
+    }
+  }
+  e = run_passes(b, s);
+  if (e != cudaSuccess) return bfail(FFTENKF_ECUDA, std::string("batched passes: ") + cudaGetErrorString(e));
+  if (any) {
+    for (int l = 0; l < kLanes && e == cudaSuccess; ++l) {
+      e = cudaEventRecord(b->ev_lane[l], b->lane[l]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_lane[l], 0);
+    }
+    if (e != cudaSuccess) return bfail(FFTENKF_ECUDA, std::string("join: ") + cudaGetErrorString(e));
+  }
+  return FFTENKF_OK;
 }
 
 extern "C" fftenkf_status fftenkf_plan_batched(fftenkf_batch* out, int count, const fftenkf_dims* dims) {
@@ -165,10 +227,27 @@ extern "C" fftenkf_status fftenkf_plan_batched(fftenkf_batch* out, int count, co
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_items, count * sizeof(BatchItem));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int l = 0; l < kLanes && e == cudaSuccess; ++l) {
+    e = cudaStreamCreateWithFlags(&b->lane[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_lane[l], cudaEventDisableTiming);
+  }
+  b->sub.assign(count, nullptr);
+  b->off_sub.assign(count, 0);
   if (e != cudaSuccess) {
     fftenkf_batch_destroy(b);
     return bfail(FFTENKF_ENOMEM, "batched plan allocation failed");
   }
+  // analyses large enough to fill the GPU through their own passes get a plan each; a shape
+  // the single-analysis plan does not take stays in the batched passes
+  for (int i = 0; i < count; ++i) {
+    if ((long long)dims[i].ny * dims[i].nx < kBigPoints) continue;
+    fftenkf_dims d = dims[i];
+    const uint8_t observed = 1;
+    fftenkf_plan sp = nullptr;
+    if (fftenkf_plan_create(&sp, &d, &observed) == FFTENKF_OK) b->sub[i] = sp;
+  }
+  set_last_error("");
   // workspace layout, item shapes and twiddle pointers
   size_t off = 0;
   b->off_mean.resize(count);
@@ -185,16 +264,23 @@ extern "C" fftenkf_status fftenkf_plan_batched(fftenkf_batch* out, int count, co
     it.N = dims[i].n_members;
     const size_t G = (size_t)it.ny * it.nx, line = (size_t)it.L * it.ny * sizeof(float2);
     const size_t tab = (size_t)(it.L + 1) * it.ny * sizeof(float);
-    b->off_mean[i] = off; off = rup(off + G * sizeof(float), 256);
-    b->off_A[i] = off;    off = rup(off + it.N * line, 256);
-    b->off_W[i] = off;    off = rup(off + it.N * line, 256);
-    b->off_chat[i] = off; off = rup(off + tab, 256);
-    b->off_gain[i] = off; off = rup(off + tab, 256);
     it.twL = b->d_tw + off_stage[0][it.L];
     it.twL_alt = b->d_tw + off_stage[1][it.L];
     it.twY = b->d_tw + off_stage[0][it.ny];
     it.twY_alt = b->d_tw + off_stage[1][it.ny];
     it.twX = b->d_tw + off_x[it.nx];
+    if (b->sub[i]) {   // the plan's workspace instead of the batched regions
+      size_t sb = 0;
+      fftenkf_workspace_size(b->sub[i], &sb);
+      b->off_sub[i] = off; off = rup(off + sb, 256);
+      b->off_mean[i] = b->off_A[i] = b->off_W[i] = b->off_chat[i] = b->off_gain[i] = b->off_sub[i];
+      continue;
+    }
+    b->off_mean[i] = off; off = rup(off + G * sizeof(float), 256);
+    b->off_A[i] = off;    off = rup(off + it.N * line, 256);
+    b->off_W[i] = off;    off = rup(off + it.N * line, 256);
+    b->off_chat[i] = off; off = rup(off + tab, 256);
+    b->off_gain[i] = off; off = rup(off + tab, 256);
   }
   b->ws_bytes = off;
   for (int pass = 0; pass < kBPassCount; ++pass) {
@@ -212,6 +298,13 @@ extern "C" fftenkf_status fftenkf_batch_destroy(fftenkf_batch b) {
   if (!b) return FFTENKF_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (fftenkf_plan sp : b->sub)
+    if (sp) fftenkf_plan_destroy(sp);
+  for (int l = 0; l < kLanes; ++l) {
+    if (b->lane[l]) cudaStreamDestroy(b->lane[l]);
+    if (b->ev_lane[l]) cudaEventDestroy(b->ev_lane[l]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   for (int p = 0; p < kBPassCount; ++p)
     if (b->d_units[p]) cudaFree(b->d_units[p]);
   if (b->d_items) cudaFree(b->d_items);
@@ -236,7 +329,9 @@ static fftenkf_status bind(fftenkf_batch b, void* const* ens, const float* const
     if (((uintptr_t)ens[i] | (uintptr_t)data[i] | (uintptr_t)pert[i] | (uintptr_t)rhat[i]) % 16)
       return bfail(FFTENKF_EINVAL, "item pointers must be 16-byte aligned");
     BatchItem& it = b->items[i];
-    changed |= it.ens != ens[i] || it.data != data[i] || it.pert != pert[i] || it.rhat != rhat[i];
+    const bool moved = it.ens != ens[i] || it.data != data[i] || it.pert != pert[i] || it.rhat != rhat[i];
+    changed |= moved;
+    if (b->sub[i] && moved) b->sub_dirty = true;   // its kernels take the pointers by value
     it.ens = ens[i];
     it.data = data[i];
     it.pert = pert[i];
@@ -247,6 +342,7 @@ static fftenkf_status bind(fftenkf_batch b, void* const* ens, const float* const
     it.chat = reinterpret_cast<float*>(ws + b->off_chat[i]);
     it.gain = reinterpret_cast<float*>(ws + b->off_gain[i]);
   }
+  if (ws != b->bound_ws) b->sub_dirty = true;
   b->bound_ws = ws;
   b->items_dirty |= changed;
   return FFTENKF_OK;
@@ -284,13 +380,23 @@ extern "C" fftenkf_status fftenkf_analyze_batched(fftenkf_batch b, void* const* 
     if (e != cudaSuccess) return bfail(FFTENKF_ECUDA, std::string("item table: ") + cudaGetErrorString(e));
     b->items_dirty = false;
   }
+  if (b->exec && b->sub_dirty) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
   if (!b->exec) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    fftenkf_status rs = FFTENKF_OK;
+    std::string rmsg;
     if (e == cudaSuccess) {
-      cudaError_t le = run_passes(b, b->cap);
+      rs = run_all(b, ensembles, data, perturbations, rhat, ws, b->cap);
+      if (rs != FFTENKF_OK) rmsg = fftenkf_last_error();
       e = cudaStreamEndCapture(b->cap, &g);
-      if (le != cudaSuccess) e = le;
+    }
+    if (rs != FFTENKF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(rs, "graph capture: " + rmsg);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
     if (g) cudaGraphDestroy(g);
@@ -298,6 +404,7 @@ extern "C" fftenkf_status fftenkf_analyze_batched(fftenkf_batch b, void* const* 
       b->exec = nullptr;
       return bfail(FFTENKF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
+    b->sub_dirty = false;
   }
   e = cudaGraphLaunch(b->exec, s);
   if (e != cudaSuccess) return bfail(FFTENKF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
@@ -403,6 +510,13 @@ extern "C" fftenkf_status fftenkf_batch_last_device_status(fftenkf_batch b, void
   e = cudaMemcpy(&word, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e != cudaSuccess) return bfail(FFTENKF_ECUDA, std::string("status word: ") + cudaGetErrorString(e));
+  fftenkf_status worst = FFTENKF_OK;
+  for (fftenkf_plan sp : b->sub) {   // the analyses on their own plans
+    if (!sp) continue;
+    const fftenkf_status st = fftenkf_last_device_status(sp, stream);
+    if (st != FFTENKF_OK && worst == FFTENKF_OK) worst = st;
+  }
   if (word & kStatusNonFinite) return bfail(FFTENKF_ENONFINITE, "non-finite spectral covariance");
+  if (worst != FFTENKF_OK) return bfail(worst, "an analysis on its own plan: " + std::string(fftenkf_last_error()));
   return FFTENKF_OK;
 }

@@ -89,3 +89,36 @@ def test_batched_rejects_bad_items(abi):
         abi.fftenkf_plan_batched([(64, 64, 5), (2048, 64, 5)], abi.FFTENKF_F32)
     with pytest.raises(abi.FftEnkfError):
         abi.fftenkf_plan_batched([(64, 64, 1)], abi.FFTENKF_F32)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_batched_planned_and_persistent_items_together(abi, storage):
+    """Analyses of at least 512 x 256 points run on their own plans on graph branches, the
+    others in the persistent passes: a mix of both (fused and separate column passes among
+    the planned ones), replayed with new pointers (a new capture), every item against the
+    oracle on the same rounded inputs."""
+    specs = [(512, 512, 5), (64, 64, 5), (512, 1024, 3), (384, 768, 4), (96, 192, 6), (256, 256, 2)]
+    items = []
+    for i, (ny, nx, N) in enumerate(specs):
+        S = fields.se_spectrum(ny, nx, 3.0 + 2 * i, 1.0)
+        rh = np.full((1, ny, nx // 2 + 1), 0.05 + 0.05 * i)
+        items.append(fields.make_problem(ny, nx, N, [S], [1], rh, seed=700 + i, storage=storage))
+    dt = torch.float32 if storage == "f32" else torch.bfloat16
+    code = abi.FFTENKF_F32 if storage == "f32" else abi.FFTENKF_BF16
+    tol = TOL32 if storage == "f32" else 5e-3
+    b = abi.fftenkf_plan_batched([(p.ny, p.nx, p.N) for p in items], code)
+    ws = torch.empty(abi.fftenkf_batch_workspace_size(b), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        dev = []
+        for p in items:
+            dev.append(dict(ens=torch.from_numpy(p.ensemble[0]).cuda().to(dt).contiguous(),
+                            data=torch.from_numpy(p.data[0].astype(np.float32)).cuda().contiguous(),
+                            pert=torch.from_numpy(p.perturbations[:, 0]).cuda().to(dt).contiguous(),
+                            rhat=torch.from_numpy(p.rhat[0]).cuda().contiguous()))
+        _run(abi, b, dev, ws)
+        for p, d in zip(items, dev):
+            ref = enkf.analyze(p.ensemble, p.data, p.perturbations, p.rhat, p.observed)[0]
+            got = d["ens"].float().cpu().numpy().astype(np.float64)
+            assert _rel(got, ref) <= tol, (p.ny, p.nx, p.N)
+            assert _rel(got - p.ensemble[0], ref - p.ensemble[0]) <= 10 * tol, (p.ny, p.nx, p.N)
+    abi.fftenkf_batch_destroy(b)
