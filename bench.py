@@ -690,10 +690,10 @@ def run_ours(a):
     # copies on one stream, the analysis on the compute stream, device -> host on a third, so
     # that step i+1's input copy overlaps step i's analysis and result copy and waits only for the
     # result copy of step i+1-NB.  The host link (about 211 GB/s in, 193 out, 340 both ways on
-    # this machine) bounds a step at (in + out bytes) / 340 GB/s.
+    # this machine, whatever the number of streams) bounds a step at (in + out bytes) / 340 GB/s.
     e2e = None
     if not a.no_e2e and a.e2e_steps > 0:
-        NB = 3
+        NB = 2
         h_in = [t.cpu().pin_memory() for t in (prob.ensemble, prob.data, prob.perturbations, prob.rhat)]
         h_out = [torch.empty_like(h_in[0]).pin_memory() for _ in range(NB)]
         d_in = [[torch.empty_like(t) for t in (prob.ensemble, prob.data, prob.perturbations, prob.rhat)]
