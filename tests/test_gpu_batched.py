@@ -122,3 +122,25 @@ def test_batched_planned_and_persistent_items_together(abi, storage):
             assert _rel(got, ref) <= tol, (p.ny, p.nx, p.N)
             assert _rel(got - p.ensemble[0], ref - p.ensemble[0]) <= 10 * tol, (p.ny, p.nx, p.N)
     abi.fftenkf_batch_destroy(b)
+
+
+def test_batched_status_reports_a_planned_item(abi):
+    """A non-finite member in an analysis that runs on its own plan is reported by the batch's
+    status read-out (ENONFINITE), as one in the persistent passes is."""
+    specs = [(512, 512, 4), (64, 64, 4)]
+    items = []
+    for i, (ny, nx, N) in enumerate(specs):
+        S = fields.se_spectrum(ny, nx, 4.0, 1.0)
+        items.append(fields.make_problem(ny, nx, N, [S], [1], np.full((1, ny, nx // 2 + 1), 0.1), seed=900 + i,
+                                         storage="f32"))
+    b = abi.fftenkf_plan_batched([(p.ny, p.nx, p.N) for p in items], abi.FFTENKF_F32)
+    ws = torch.empty(abi.fftenkf_batch_workspace_size(b), dtype=torch.uint8, device="cuda")
+    dev = _upload(items)
+    dev[0]["ens"][1, 7, 9] = float("inf")
+    abi.fftenkf_analyze_batched(b, [d["ens"] for d in dev], [d["data"] for d in dev], [d["pert"] for d in dev],
+                                [d["rhat"] for d in dev], ws, 0)
+    assert abi.fftenkf_batch_last_device_status(b, 0) == abi.FFTENKF_ENONFINITE
+    dev = _upload(items)   # finite again: OK and correct
+    _run(abi, b, dev, ws)
+    assert _check(items, dev) <= TOL32
+    abi.fftenkf_batch_destroy(b)
