@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -279,12 +280,19 @@ OTHER_SOURCES = ("sine_api.cu", "batch_api.cu", "batch.cuh", "k_batch.cuh", "k_b
                  "morph_api.cu", "static_api.cu")
 
 
+def _code_only(text):
+    """A source without its comments and blank space: a comment edit leaves the kernels unchanged."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1001_1588_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")) and f not in OTHER_SOURCES and not f.startswith("k_batch_"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            h.update(_code_only(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

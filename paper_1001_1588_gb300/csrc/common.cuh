@@ -209,7 +209,7 @@ cudaError_t launch_row_inv(const RowInvParams& p, int n_fields, cudaStream_t s);
 // rows per item of the inverse row pass for (nx/2, schedule, ny, nx, storage bytes); 0 = unsupported
 int row_inv_rows(int L, int vsel, int ny, int nx, int es);
 // tensor map of the increment row spectra [fields][L][ny] for the inverse row pass's tile
-// loads (R rows x box_cols columns per copy); false if R < 2 or the driver refuses it
+// loads (R rows x box_cols columns per copy); false if R < 2 or cuTensorMapEncodeTiled rejects it
 bool encode_increment_map(CUtensorMap* out, const float2* S, int fields, int ny, int L, int R, int box_cols);
 cudaError_t launch_col_stats(const ColStatsParams& p, cudaStream_t s);
 cudaError_t launch_col_update(const ColUpdParams& p, cudaStream_t s);
