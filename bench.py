@@ -699,13 +699,12 @@ def run_ours(a):
     # that step i+1's input copy overlaps step i's analysis and result copy and waits only for the
     # result copy of step i+1-NB.  The host link (about 211 GB/s in, 193 out, 340 both ways on
     # this machine, whatever the number of streams) bounds a step at (in + out bytes) / 340 GB/s.
-    e2e = None
-    if not a.no_e2e and a.e2e_steps > 0:
-        NB = 2
-        h_in = [t.cpu().pin_memory() for t in (prob.ensemble, prob.data, prob.perturbations, prob.rhat)]
+    def e2e_run(host_src, analyze_fn, NB=2):
+        """ms per step, bytes in and out per step of the streamed pipeline over host copies of
+        host_src (the first is the ensemble, analysed in place and copied back)."""
+        h_in = [t.cpu().pin_memory() for t in host_src]
         h_out = [torch.empty_like(h_in[0]).pin_memory() for _ in range(NB)]
-        d_in = [[torch.empty_like(t) for t in (prob.ensemble, prob.data, prob.perturbations, prob.rhat)]
-                for _ in range(NB)]
+        d_in = [[torch.empty_like(t) for t in host_src] for _ in range(NB)]
         bi = sum(t.numel() * t.element_size() for t in h_in)
         bo = h_out[0].numel() * h_out[0].element_size()
         s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -723,7 +722,7 @@ def run_ours(a):
                     dt.copy_(ht, non_blocking=True)
                 ev_in[b].record(s_in)
             stream.wait_event(ev_in[b])
-            plan.analyze(*d_in[b], stream=stream)
+            analyze_fn(d_in[b], i)
             ev_done[b].record(stream)
             s_out.wait_event(ev_done[b])
             with torch.cuda.stream(s_out):
@@ -744,12 +743,28 @@ def run_ours(a):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ems = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
+        del d_in, h_in, h_out
+        return ems, bi, bo
+
+    e2e = None
+    e2e_seeded = None
+    if not a.no_e2e and a.e2e_steps > 0:
+        NB = 2
+        ems, bi, bo = e2e_run((prob.ensemble, prob.data, prob.perturbations, prob.rhat),
+                              lambda d, i: plan.analyze(*d, stream=stream), NB)
         e2e = {"value": job_throughput(float(ny) * nx * Nm * a.e2e_steps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": a.e2e_steps,
                "ms_per_step": ems / a.e2e_steps,
                "pipeline": "inputs in %d device buffers; host->device, analysis and device->host on three "
                            "streams, step i+1's input copy overlapping step i" % NB}
-        del d_in, h_in, h_out
+        if not a.no_seeded:
+            # the same pipeline with the perturbations drawn by the library: no perturbation upload
+            ems, bi, bo = e2e_run((prob.ensemble, prob.data, prob.rhat),
+                                  lambda d, i: plan.analyze_seeded(d[0], d[1], d[2], 777 + i, stream=stream), NB)
+            e2e_seeded = {"value": job_throughput(float(ny) * nx * Nm * a.e2e_steps, world, ems), "unit": UNIT,
+                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": a.e2e_steps,
+                          "ms_per_step": ems / a.e2e_steps,
+                          "note": "fftenkf_analyze_seeded: ensemble, data and rhat uploaded, perturbations drawn"}
 
     # the same analyses with the perturbations drawn by the library (fftenkf_analyze_seeded)
     equal_rmse = None
@@ -803,6 +818,7 @@ def run_ours(a):
             "fused_schedule": fused_schedule,
             "clocks": clk.summary(),
             "e2e": e2e,
+            "e2e_seeded": e2e_seeded,
             "gpu_launches": sum(v["launches"] for v in per_pass.values()),
             "cpu_baseline": cpu,
             "cufft_reference": cufft,
