@@ -137,7 +137,7 @@ fftenkf_status fftenkf_analyze_seeded(fftenkf_plan plan, void* ensemble, const f
  * not call cudaMalloc -- e.g. a host framework that owns every device
  * allocation through its own pool, or a latency-critical loop that cannot
  * afford cudaMalloc's implicit synchronisation -- it needs no plan and no
- * workspace: all scratch (twiddle tables, mean, row spectra, covariance table,
+ * workspace: all scratch (twiddle tables, row spectra, covariance table,
  * status word) comes from one static device array of 64 MiB that every GPU
  * loading this library holds until the process exits.  It allocates nothing
  * and calls no allocating routine.
@@ -145,7 +145,7 @@ fftenkf_status fftenkf_analyze_seeded(fftenkf_plan plan, void* ensemble, const f
  *   spectrum_out  [ny][nx/2+1] device doubles: the same single-block table that
  *                 fftenkf_estimate_spectrum writes (unitary scaling)
  * Sizes follow the plan limits; a problem whose scratch exceeds the array
- * (about N (nx/2) ny 8 + ny nx 4 bytes plus small tables > 64 MiB) returns
+ * (about N (nx/2) ny 8 bytes plus small tables > 64 MiB) returns
  * FFTENKF_EUNSUPPORTED with a message giving the bytes needed.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress, with
  * that device current) and caches it, so make that first call before any
