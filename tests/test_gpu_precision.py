@@ -78,3 +78,35 @@ def test_bounded_wait_expiry_then_recovery():
     plan.close()
     ref = enkf.analyze(p.ensemble, p.data, p.perturbations, p.rhat, p.observed)
     assert gu.rel_l2(ua, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("ny,nx", [(64, 64), (512, 64)])      # column-statistics epilogue; fused column pass
+@pytest.mark.parametrize("ratio", [1e-6, 1e-9])
+def test_gain_band_small_chat_over_rhat(ny, nx, ratio):
+    """The gain quotient where chat/rhat is tiny, isolated: white members of standard deviation
+    `ratio` (chat about ratio^2), rhat = 1e30 below |k| = ny/4 (no update there) and `ratio` above
+    (chat/rhat about `ratio`), white data, no perturbations.  The whole increment then lies in the
+    high-k band and is about `ratio` times the innovation (as large as the members, so the FP32
+    output keeps its digits), and FFT round-off of other bands cannot hide an error of the FP32
+    quotient there; the increment must match the FP64 oracle to 1e-5 (relative L2), and its low
+    band must stay 0."""
+    from tests import gpu_util as gu
+    rng = np.random.default_rng(4242 + ny)
+    N = 5
+    ens = (ratio * rng.standard_normal((1, N, ny, nx))).astype(np.float32).astype(np.float64)
+    data = rng.standard_normal((1, ny, nx)).astype(np.float32).astype(np.float64)
+    pert = np.zeros((N, 1, ny, nx))
+    kk = fields.radial_wavenumber_half(ny, nx)
+    rhat = np.where(kk < ny / 4, 1e30, ratio)[None]
+    p = fields.Problem(ny=ny, nx=nx, M=1, N=N, observed=np.array([1], np.uint8), storage="f32",
+                       ensemble=ens.astype(np.float32), data=data.astype(np.float32),
+                       perturbations=pert.astype(np.float32), rhat=rhat, truth=np.zeros((1, ny, nx)))
+    ua, st = gu.gpu_analyze(p)
+    assert st == 0
+    ref = enkf.analyze(p.ensemble, p.data, p.perturbations, p.rhat, p.observed)
+    inc, inc_ref = ua - ens, ref - ens
+    assert np.abs(inc_ref).max() > 0.1 * ratio   # the band update is there and of the expected size
+    assert gu.rel_l2(inc, inc_ref) <= 1e-5
+    low = kk < ny / 4
+    got_hat = np.fft.rfft2(inc[0, 0], norm="ortho")
+    assert np.abs(got_hat[low]).max() <= 1e-6 * np.abs(got_hat).max()
